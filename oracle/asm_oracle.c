@@ -1,0 +1,642 @@
+/*
+ * asm_oracle.c -- plain FP64 CPU oracle of the average spectrum method with
+ * blocked modes sampling (Ghanem & Koch, arXiv:1912.01379).
+ *
+ * TEST INFRASTRUCTURE ONLY (see asm_oracle.h).  Slow on purpose: every block
+ * visit recomputes the data seen by the block from scratch and every move
+ * recomputes the mode coordinate by a dot product, exactly as Sec. IV.D counts
+ * the work.  No blocking, fusion or incremental bookkeeping.
+ *
+ * Readings of the paper that this file fixes (all also listed in the design doc):
+ *  R1 moves draw delta = e' - e from the 1-D conditional with ONE uniform u
+ *     through the inverse CDF of the truncated normal (Sec. IV.A cites a
+ *     rejection sampler; an inverse CDF samples the same distribution).
+ *  R2 zero modes (d = 0, Sec. IV.B) are flat on their interval; singular
+ *     values d <= d_1 max(M, n) 2^-52 count as zero.
+ *  R3 the bounds of Eq. modeLimits are used as delta in [max_{V>0} -f/V,
+ *     min_{V<0} -f/V]; entries |V| < 2^-40 max|V| are left out of the bounds;
+ *     after the move f is clamped at 0 so A >= 0 holds exactly.
+ *  R4 sweep order: modes in index order (largest d first) within a block,
+ *     blocks left to right; one level per sweep drawn uniformly (Sec. IV.C).
+ *  R5 random numbers: Philox4x64-10, key {seed, 0}; move t of sweep s of chain
+ *     q of problem p uses word t mod 4 of ctr {t div 4, s, q, p}; the level of
+ *     sweep s uses word 0 of ctr {2^64-1, s, 0, p}; u = (w>>12 + 1/2) 2^-52.
+ *  R6 sign convention: the largest |component| of every V_j is positive
+ *     (lowest index on ties).
+ */
+#include "asm_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORA_SQRT2 1.41421356237309504880
+#define ORA_SQRT_2_OVER_PI 0.79788456080286535588
+#define ORA_INV_SQRT_PI 0.56418958354775628695
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x64-10 from its published definition (Salmon et al., SC'11,       */
+/* Sec. 4.3): 10 rounds of two 64x64->128 multiplies; the key is bumped by   */
+/* the Weyl constants before every round after the first.                   */
+/* ------------------------------------------------------------------------ */
+void ora_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        unsigned __int128 p0 = (unsigned __int128)M0 * x0;
+        unsigned __int128 p1 = (unsigned __int128)M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static double ora_u01(uint64_t w) { return ((double)(w >> 12) + 0.5) * 0x1p-52; }
+
+/* ------------------------------------------------------------------------ */
+/* Normal distribution.  erfc comes from the C library; erfcx for x >= 2   */
+/* from its continued fraction (Abramowitz & Stegun 7.1.14).               */
+/* ------------------------------------------------------------------------ */
+double ora_norm_cdf(double z) { return 0.5 * erfc(-z / ORA_SQRT2); }
+static double ora_q(double z) { return 0.5 * erfc(z / ORA_SQRT2); }
+
+double ora_erfcx(double x)
+{
+    if (x < 0.0) return 2.0 * exp(x * x) - ora_erfcx(-x);
+    if (x < 2.0) return exp(x * x) * erfc(x);
+    /* Laplace continued fraction (Abramowitz & Stegun 7.1.14), evaluated
+     * backwards from a fixed depth: 1/(sqrt(pi) (x + (1/2)/(x + 1/(x + ...)))) */
+    double t = x;
+    for (int k = 120; k >= 1; --k) t = x + 0.5 * k / t;
+    return ORA_INV_SQRT_PI / t;
+}
+
+double ora_log_q(double x)
+{
+    /* Q(x) = exp(-x^2/2) erfcx(x/sqrt2) / 2 */
+    return log(0.5 * ora_erfcx(x / ORA_SQRT2)) - 0.5 * x * x;
+}
+
+/* log Phi(x) and phi(x)/Phi(x) without underflow. */
+static double ora_log_phi_cdf(double x)
+{
+    if (x < 0.0) return log(0.5 * ora_erfcx(-x / ORA_SQRT2)) - 0.5 * x * x;
+    return log1p(-ora_q(x));
+}
+static double ora_mills_inv(double x)
+{
+    if (x < 0.0) return ORA_SQRT_2_OVER_PI / ora_erfcx(-x / ORA_SQRT2);
+    return exp(-0.5 * x * x) / (sqrt(2.0 * M_PI) * ora_norm_cdf(x));
+}
+
+/* Phi^{-1}(p): rational start (Abramowitz & Stegun 26.2.23) refined by
+ * Newton's method on log Phi(x) = log p, which converges monotonically
+ * because log Phi is concave. */
+double ora_norm_quantile(double p)
+{
+    if (!(p > 0.0)) return -INFINITY;
+    if (!(p < 1.0)) return INFINITY;
+    if (p > 0.5) return -ora_norm_quantile(1.0 - p);
+    double t = sqrt(-2.0 * log(p));
+    double x = -(t - (2.515517 + 0.802853 * t + 0.010328 * t * t) /
+                     (1.0 + 1.432788 * t + 0.189269 * t * t + 0.001308 * t * t * t));
+    double lp = log(p);
+    for (int it = 0; it < 100; ++it) {
+        double g = ora_log_phi_cdf(x) - lp;
+        double dx = -g / ora_mills_inv(x);
+        x += dx;
+        if (fabs(dx) <= 1e-16 * fmax(1.0, fabs(x))) break;
+    }
+    return x;
+}
+
+/* Right tail: x ~ N(0,1) restricted to [a, b], 0 <= a < b <= inf, by the
+ * inverse CDF Q(x) = (1-u) Q(a) + u Q(b).  Returns y = x - a >= 0. */
+static double ora_right_tail(double a, double b, double u, int *capped)
+{
+    double y;
+    if (a < 5.0) {
+        double qa = ora_q(a), qb = isinf(b) ? 0.0 : ora_q(b);
+        double q = (1.0 - u) * qa + u * qb;
+        y = -ora_norm_quantile(q) - a;
+    } else {
+        /* log space: log Q(a + y) - log Q(a) = log((1-u) + u Q(b)/Q(a)) */
+        double la = ora_log_q(a);
+        double r = isinf(b) ? 0.0 : exp(ora_log_q(b) - la);
+        /* both forms are exact in 1 - u (u is on the 2^-52 grid); each keeps
+         * the relative accuracy of the small quantity in its own regime */
+        double dt = u < 0.5 ? log1p(-u * (1.0 - r)) : log((1.0 - u) + u * r);
+        double exa = ora_erfcx(a / ORA_SQRT2);
+        y = -dt / a;
+        int it;
+        for (it = 0; it < 100; ++it) {
+            double exy = ora_erfcx((a + y) / ORA_SQRT2);
+            double g = log(exy / exa) - y * (a + 0.5 * y) - dt;
+            double gp = -ORA_SQRT_2_OVER_PI / exy;
+            double step = g / gp;
+            y -= step;
+            if (fabs(step) <= 1e-14 * (y + 1.0 / a)) break;
+        }
+        if (it == 100 && capped) ++*capped;
+    }
+    if (y < 0.0) y = 0.0;
+    if (y > b - a) y = b - a;
+    return y;
+}
+
+static double ora_truncnorm_impl(double mu, double sigma, double lo, double hi, double u,
+                                 int *capped)
+{
+    if (!(hi > lo)) return lo;
+    double alpha = (lo - mu) / sigma, beta = (hi - mu) / sigma;
+    double d;
+    if (alpha >= 0.0) {
+        d = lo + sigma * ora_right_tail(alpha, beta, u, capped);
+    } else if (beta <= 0.0) {
+        d = hi - sigma * ora_right_tail(-beta, -alpha, 1.0 - u, capped);
+    } else {
+        double pa = ora_norm_cdf(alpha), pb = ora_norm_cdf(beta);
+        double p = (1.0 - u) * pa + u * pb;
+        double x;
+        if (p <= 0.5) {
+            x = ora_norm_quantile(p);
+        } else {
+            double q = (1.0 - u) * ora_q(alpha) + u * ora_q(beta);
+            x = -ora_norm_quantile(q);
+        }
+        d = mu + sigma * x;
+    }
+    if (d < lo) d = lo;
+    if (d > hi) d = hi;
+    return d;
+}
+
+double ora_truncnorm(double mu, double sigma, double lo, double hi, double u)
+{
+    return ora_truncnorm_impl(mu, sigma, lo, hi, u, &(int){0});
+}
+
+/* ------------------------------------------------------------------------ */
+/* Linear algebra                                                           */
+/* ------------------------------------------------------------------------ */
+int ora_cholesky(int n, const double *C, double *L)
+{
+    memset(L, 0, sizeof(double) * (size_t)n * n);
+    for (int j = 0; j < n; ++j) {
+        double s = C[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        if (!(s > 0.0)) return -2;
+        double ljj = sqrt(s);
+        L[(size_t)j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = C[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)i * n + j] = t / ljj;
+        }
+    }
+    return 0;
+}
+
+/* One-sided (Hestenes) Jacobi: rotate column pairs of W = A until all pairs
+ * are orthogonal; then s_j = |W_j|, U_j = W_j / s_j and V collects the
+ * rotations.  For n > m the n - m surplus columns converge to zero and V
+ * still is a full orthogonal basis, which gives the zero modes of Sec. IV.B. */
+int ora_jacobi_svd(int m, int n, const double *A, double *s, double *U, double *V)
+{
+    double *W = (double *)malloc(sizeof(double) * (size_t)m * n);  /* column-major */
+    double *Z = (double *)malloc(sizeof(double) * (size_t)n * n);  /* column-major */
+    if (!W || !Z) { free(W); free(Z); return -1; }
+    double norm2 = 0.0;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) {
+            W[(size_t)j * m + i] = A[(size_t)i * n + j];
+            norm2 += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Z[(size_t)j * n + i] = (i == j) ? 1.0 : 0.0;
+    int sweep, converged = 0;
+    for (sweep = 1; sweep <= 80 && !converged; ++sweep) {
+        int rotated = 0;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double *wp = W + (size_t)p * m, *wq = W + (size_t)q * m;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = 0; i < m; ++i) {
+                    al += wp[i] * wp[i];
+                    be += wq[i] * wq[i];
+                    ga += wp[i] * wq[i];
+                }
+                if (fabs(ga) <= 1e-15 * sqrt(al * be) || fabs(ga) <= 1e-30 * norm2) continue;
+                double zeta = (be - al) / (2.0 * ga);
+                double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                for (int i = 0; i < m; ++i) {
+                    double a = wp[i], b = wq[i];
+                    wp[i] = c * a - sn * b;
+                    wq[i] = sn * a + c * b;
+                }
+                double *zp = Z + (size_t)p * n, *zq = Z + (size_t)q * n;
+                for (int i = 0; i < n; ++i) {
+                    double a = zp[i], b = zq[i];
+                    zp[i] = c * a - sn * b;
+                    zq[i] = sn * a + c * b;
+                }
+                rotated = 1;
+            }
+        if (!rotated) converged = 1;
+    }
+    /* column norms, then sort descending (selection sort: n is small) */
+    int *ord = (int *)malloc(sizeof(int) * n);
+    double *sv = (double *)malloc(sizeof(double) * n);
+    for (int j = 0; j < n; ++j) {
+        double t = 0.0;
+        for (int i = 0; i < m; ++i) t += W[(size_t)j * m + i] * W[(size_t)j * m + i];
+        sv[j] = sqrt(t);
+        ord[j] = j;
+    }
+    for (int a = 0; a < n; ++a) {
+        int best = a;
+        for (int b = a + 1; b < n; ++b)
+            if (sv[ord[b]] > sv[ord[best]]) best = b;
+        int tmp = ord[a]; ord[a] = ord[best]; ord[best] = tmp;
+    }
+    for (int a = 0; a < n; ++a) {
+        int j = ord[a];
+        double *z = Z + (size_t)j * n, *w = W + (size_t)j * m;
+        /* sign convention R6 */
+        int imax = 0;
+        for (int i = 1; i < n; ++i)
+            if (fabs(z[i]) > fabs(z[imax])) imax = i;
+        double sg = z[imax] < 0.0 ? -1.0 : 1.0;
+        s[a] = sv[j];
+        for (int i = 0; i < n; ++i) V[(size_t)i * n + a] = sg * z[i];
+        for (int i = 0; i < m; ++i) U[(size_t)i * n + a] = sv[j] > 0.0 ? sg * w[i] / sv[j] : 0.0;
+    }
+    free(ord); free(sv); free(W); free(Z);
+    return converged ? sweep - 1 : -2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Problem set-up: whitening (Sec. IV, C^{-1} = T^T T with T = L^{-1}) and   */
+/* the SVD of every block of every level (Sec. IV.B-C).                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int start, n, np;    /* first column, width, number of U columns min(M, n) */
+    double *d;           /* n singular values, 0 for zero modes (R2) */
+    double *V;           /* n x n mode-major */
+    double *U;           /* np x M mode-major */
+} ora_block;
+
+struct ora_problem {
+    int M, N, n_levels;
+    int *level_nblocks, *level_first;
+    int n_blocks;
+    ora_block *blk;
+    double *Kt, *gt;     /* whitened kernel (M x N row-major) and data */
+};
+
+void ora_free(ora_problem *p)
+{
+    if (!p) return;
+    for (int b = 0; b < p->n_blocks; ++b) {
+        free(p->blk[b].d); free(p->blk[b].V); free(p->blk[b].U);
+    }
+    free(p->blk); free(p->level_nblocks); free(p->level_first);
+    free(p->Kt); free(p->gt);
+    free(p);
+}
+
+static int ora_block_svd(const ora_problem *p, ora_block *b)
+{
+    int M = p->M, n = b->n;
+    double *A = (double *)malloc(sizeof(double) * (size_t)M * n);
+    double *s = (double *)malloc(sizeof(double) * n);
+    double *U = (double *)malloc(sizeof(double) * (size_t)M * n);
+    double *V = (double *)malloc(sizeof(double) * (size_t)n * n);
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = p->Kt[(size_t)i * p->N + b->start + j];
+    int rc = ora_jacobi_svd(M, n, A, s, U, V);
+    if (rc < 0) { free(A); free(s); free(U); free(V); return -1; }
+    b->np = M < n ? M : n;
+    b->d = (double *)calloc(n, sizeof(double));
+    b->V = (double *)malloc(sizeof(double) * (size_t)n * n);
+    b->U = (double *)calloc((size_t)b->np * M, sizeof(double));
+    double thr = s[0] * (double)(M > n ? M : n) * 0x1p-52;
+    for (int j = 0; j < n; ++j) {
+        b->d[j] = (j < b->np && s[j] > thr) ? s[j] : 0.0;
+        for (int i = 0; i < n; ++i) b->V[(size_t)j * n + i] = V[(size_t)i * n + j];
+        if (j < b->np && b->d[j] > 0.0)
+            for (int m = 0; m < M; ++m) b->U[(size_t)j * M + m] = U[(size_t)m * n + j];
+    }
+    free(A); free(s); free(U); free(V);
+    /* R2 properness: along a zero mode the interval must be finite on both
+     * sides, i.e. the mode vector must change sign. */
+    for (int j = 0; j < n; ++j) {
+        if (b->d[j] > 0.0) continue;
+        const double *v = b->V + (size_t)j * n;
+        double vmax = 0.0;
+        for (int i = 0; i < n; ++i) vmax = fmax(vmax, fabs(v[i]));
+        int pos = 0, neg = 0;
+        for (int i = 0; i < n; ++i) {
+            if (fabs(v[i]) < 0x1p-40 * vmax) continue;
+            if (v[i] > 0.0) pos = 1;
+            if (v[i] < 0.0) neg = 1;
+        }
+        if (!(pos && neg)) return -4;
+    }
+    return 0;
+}
+
+ora_problem *ora_setup(int M, int N, const double *K, const double *G, const double *C,
+                       int n_levels, const int *level_nblocks, const int *block_start, int *err)
+{
+    *err = 0;
+    if (M < 1 || N < 1 || n_levels < 1) { *err = -1; return NULL; }
+    for (long i = 0; i < (long)M * N; ++i) if (!isfinite(K[i])) { *err = -3; return NULL; }
+    for (int i = 0; i < M; ++i) if (!isfinite(G[i])) { *err = -3; return NULL; }
+    for (long i = 0; i < (long)M * M; ++i) if (!isfinite(C[i])) { *err = -3; return NULL; }
+    ora_problem *p = (ora_problem *)calloc(1, sizeof(ora_problem));
+    p->M = M; p->N = N; p->n_levels = n_levels;
+    p->level_nblocks = (int *)malloc(sizeof(int) * n_levels);
+    p->level_first = (int *)malloc(sizeof(int) * n_levels);
+    int nb = 0;
+    for (int l = 0; l < n_levels; ++l) {
+        if (level_nblocks[l] < 1) { *err = -1; ora_free(p); return NULL; }
+        p->level_nblocks[l] = level_nblocks[l];
+        p->level_first[l] = nb;
+        nb += level_nblocks[l];
+    }
+    p->n_blocks = nb;
+    p->blk = (ora_block *)calloc(nb, sizeof(ora_block));
+    for (int l = 0; l < n_levels; ++l) {
+        const int *st = block_start + p->level_first[l];
+        for (int b = 0; b < level_nblocks[l]; ++b) {
+            int s0 = st[b], s1 = (b + 1 < level_nblocks[l]) ? st[b + 1] : N;
+            if ((b == 0 && s0 != 0) || s1 <= s0 || s1 > N) { *err = -1; ora_free(p); return NULL; }
+            p->blk[p->level_first[l] + b].start = s0;
+            p->blk[p->level_first[l] + b].n = s1 - s0;
+        }
+    }
+    /* whitening: C = L L^T, T = L^{-1}, K~ = T K, g~ = T G (forward substitution) */
+    double *L = (double *)malloc(sizeof(double) * (size_t)M * M);
+    if (ora_cholesky(M, C, L) != 0) { free(L); *err = -2; ora_free(p); return NULL; }
+    p->Kt = (double *)malloc(sizeof(double) * (size_t)M * N);
+    p->gt = (double *)malloc(sizeof(double) * M);
+    for (int i = 0; i < M; ++i) {
+        for (int j = 0; j < N; ++j) {
+            double t = K[(size_t)i * N + j];
+            for (int k = 0; k < i; ++k) t -= L[(size_t)i * M + k] * p->Kt[(size_t)k * N + j];
+            p->Kt[(size_t)i * N + j] = t / L[(size_t)i * M + i];
+        }
+        double t = G[i];
+        for (int k = 0; k < i; ++k) t -= L[(size_t)i * M + k] * p->gt[k];
+        p->gt[i] = t / L[(size_t)i * M + i];
+    }
+    free(L);
+    for (int b = 0; b < nb; ++b) {
+        int rc = ora_block_svd(p, &p->blk[b]);
+        if (rc != 0) { *err = rc == -4 ? -4 : -1; ora_free(p); return NULL; }
+    }
+    return p;
+}
+
+void ora_sizes(const ora_problem *p, long *n_d, long *n_V, long *n_U)
+{
+    long a = 0, b = 0, c = 0;
+    for (int k = 0; k < p->n_blocks; ++k) {
+        a += p->blk[k].n;
+        b += (long)p->blk[k].n * p->blk[k].n;
+        c += (long)p->blk[k].np * p->M;
+    }
+    *n_d = a; *n_V = b; *n_U = c;
+}
+
+void ora_export(const ora_problem *p, double *Kt, double *gt, double *d, double *V, double *U)
+{
+    memcpy(Kt, p->Kt, sizeof(double) * (size_t)p->M * p->N);
+    memcpy(gt, p->gt, sizeof(double) * p->M);
+    for (int k = 0; k < p->n_blocks; ++k) {
+        const ora_block *b = &p->blk[k];
+        memcpy(d, b->d, sizeof(double) * b->n); d += b->n;
+        memcpy(V, b->V, sizeof(double) * (size_t)b->n * b->n); V += (size_t)b->n * b->n;
+        memcpy(U, b->U, sizeof(double) * (size_t)b->np * p->M); U += (size_t)b->np * p->M;
+    }
+}
+
+void ora_initial_f(const ora_problem *p, double *f0)
+{
+    /* s* = argmin_{s >= 0} | g~ - s K~ 1 |^2 */
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < p->M; ++i) {
+        double k = 0.0;
+        for (int j = 0; j < p->N; ++j) k += p->Kt[(size_t)i * p->N + j];
+        num += k * p->gt[i];
+        den += k * k;
+    }
+    double s = den > 0.0 ? num / den : 0.0;
+    if (!(s > 0.0) || !isfinite(s)) s = 1.0 / p->N;
+    for (int j = 0; j < p->N; ++j) f0[j] = s;
+}
+
+double ora_chi2(const ora_problem *p, const double *f)
+{
+    double c = 0.0;
+    for (int i = 0; i < p->M; ++i) {
+        double r = p->gt[i];
+        for (int j = 0; j < p->N; ++j) r -= p->Kt[(size_t)i * p->N + j] * f[j];
+        c += r * r;
+    }
+    return c;
+}
+
+/* Data seen by block b: h_b = U_b^T (g~ - sum_{blocks b' != b} K~_{b'} f_{b'})
+ * (Sec. IV.D: the contribution of the other blocks). */
+static void ora_block_h(const ora_problem *p, const ora_block *b, const double *f, double *gp,
+                        double *h)
+{
+    for (int i = 0; i < p->M; ++i) {
+        double t = p->gt[i];
+        for (int j = 0; j < p->N; ++j) {
+            if (j >= b->start && j < b->start + b->n) continue;
+            t -= p->Kt[(size_t)i * p->N + j] * f[j];
+        }
+        gp[i] = t;
+    }
+    for (int j = 0; j < b->np; ++j) {
+        double t = 0.0;
+        for (int i = 0; i < p->M; ++i) t += b->U[(size_t)j * p->M + i] * gp[i];
+        h[j] = t;
+    }
+}
+
+/* Interval of delta = e_j' - e_j that keeps f + delta V_j >= 0 (Eq. modeLimits, R3). */
+static void ora_bounds(const ora_block *b, int j, const double *f, double *lo, double *hi)
+{
+    const double *v = b->V + (size_t)j * b->n;
+    const double *fb = f + b->start;
+    double vmax = 0.0;
+    for (int i = 0; i < b->n; ++i) vmax = fmax(vmax, fabs(v[i]));
+    double l = -INFINITY, h = INFINITY;
+    for (int i = 0; i < b->n; ++i) {
+        if (fabs(v[i]) < 0x1p-40 * vmax) continue;
+        double fi = fb[i] > 0.0 ? fb[i] : 0.0;
+        double t = -fi / v[i];
+        if (v[i] > 0.0) { if (t > l) l = t; }
+        else { if (t < h) h = t; }
+    }
+    *lo = l; *hi = h;
+}
+
+/* Conditional of mode j of block b given the rest (Sec. IV.B-C):
+ * e_j' ~ N(h_j/d_j, 1/d_j^2), so delta ~ N(h_j/d_j - e_j, 1/d_j^2). */
+static void ora_mode_conditional(const ora_block *b, int j, const double *f, const double *h,
+                                 double *mu, double *sigma)
+{
+    const double *v = b->V + (size_t)j * b->n;
+    double e = 0.0;
+    for (int i = 0; i < b->n; ++i) e += v[i] * f[b->start + i];
+    if (b->d[j] > 0.0) {
+        *mu = h[j] / b->d[j] - e;
+        *sigma = 1.0 / b->d[j];
+    } else {
+        *mu = 0.0;
+        *sigma = 0.0;
+    }
+}
+
+int ora_conditional(const ora_problem *p, int level, int block, int j, const double *f,
+                    double *mu, double *sigma, double *lo, double *hi)
+{
+    if (level < 0 || level >= p->n_levels || block < 0 || block >= p->level_nblocks[level]) return -1;
+    const ora_block *b = &p->blk[p->level_first[level] + block];
+    if (j < 0 || j >= b->n) return -1;
+    double *gp = (double *)malloc(sizeof(double) * p->M);
+    double *h = (double *)malloc(sizeof(double) * (b->np > 0 ? b->np : 1));
+    ora_block_h(p, b, f, gp, h);
+    ora_mode_conditional(b, j, f, h, mu, sigma);
+    ora_bounds(b, j, f, lo, hi);
+    free(gp); free(h);
+    return 0;
+}
+
+static void ora_chain(const ora_problem *p, int q, double *f, long sweep0, long burn_in,
+                      long sweeps, uint64_t seed, uint64_t problem_id, double *S1, double *S2,
+                      double *trace, long *stats)
+{
+    int M = p->M, N = p->N;
+    double *gp = (double *)malloc(sizeof(double) * M);
+    double *h = (double *)malloc(sizeof(double) * (M > 0 ? M : 1));
+    const uint64_t key[2] = {seed, 0};
+    long viol = 0, degen = 0, flat = 0;
+    int capped = 0;
+    for (long s = sweep0; s < sweep0 + burn_in + sweeps; ++s) {
+        uint64_t w[4];
+        uint64_t lc[4] = {~(uint64_t)0, (uint64_t)s, 0, problem_id};
+        ora_philox4x64_10(lc, key, w);
+        int level = (int)(ora_u01(w[0]) * p->n_levels);
+        if (level >= p->n_levels) level = p->n_levels - 1;
+        for (int bi = 0; bi < p->level_nblocks[level]; ++bi) {
+            const ora_block *b = &p->blk[p->level_first[level] + bi];
+            ora_block_h(p, b, f, gp, h);
+            for (int j = 0; j < b->n; ++j) {
+                long t = b->start + j;
+                uint64_t ctr[4] = {(uint64_t)t >> 2, (uint64_t)s, (uint64_t)q, problem_id};
+                ora_philox4x64_10(ctr, key, w);
+                double u = ora_u01(w[t & 3]);
+                double mu, sigma, lo, hi, delta;
+                ora_mode_conditional(b, j, f, h, &mu, &sigma);
+                ora_bounds(b, j, f, &lo, &hi);
+                if (!(hi > lo)) {
+                    delta = 0.0;
+                    ++degen;
+                } else if (sigma == 0.0) {
+                    delta = lo + u * (hi - lo);
+                    ++flat;
+                } else {
+                    delta = ora_truncnorm_impl(mu, sigma, lo, hi, u, &capped);
+                }
+                const double *v = b->V + (size_t)j * b->n;
+                for (int i = 0; i < b->n; ++i) {
+                    double x = f[b->start + i] + delta * v[i];
+                    if (x < -1e-12 * (fabs(f[b->start + i]) + 1e-300)) ++viol;
+                    f[b->start + i] = x > 0.0 ? x : 0.0;
+                }
+            }
+        }
+        long k = s - sweep0;
+        if (k >= burn_in && S1) {
+            for (int j = 0; j < N; ++j) {
+                S1[j] += f[j];
+                S2[j] += f[j] * f[j];
+            }
+        }
+        if (trace) memcpy(trace + (size_t)k * N, f, sizeof(double) * N);
+    }
+    if (stats) {
+        stats[0] = viol; stats[1] = degen; stats[2] = flat; stats[3] = capped;
+    }
+    free(gp); free(h);
+}
+
+int ora_run_from(const ora_problem *p, int chains, const double *f_start, long sweep0,
+                 long burn_in, long sweeps, uint64_t seed, uint64_t problem_id, int n_threads,
+                 double *f_final, double *S1, double *S2, double *chi2_final,
+                 double *trace, int n_traced, long *stats)
+{
+    int N = p->N;
+    long tot[4] = {0, 0, 0, 0};
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+#pragma omp parallel
+    {
+        long loc[4] = {0, 0, 0, 0};
+        double *f = (double *)malloc(sizeof(double) * N);
+        double *s1 = (double *)malloc(sizeof(double) * N);
+        double *s2 = (double *)malloc(sizeof(double) * N);
+#pragma omp for schedule(dynamic, 1)
+        for (int q = 0; q < chains; ++q) {
+            long st[4] = {0, 0, 0, 0};
+            memcpy(f, f_start + (size_t)q * N, sizeof(double) * N);
+            memset(s1, 0, sizeof(double) * N);
+            memset(s2, 0, sizeof(double) * N);
+            double *tr = (trace && q < n_traced) ? trace + (size_t)q * (burn_in + sweeps) * N : NULL;
+            ora_chain(p, q, f, sweep0, burn_in, sweeps, seed, problem_id, s1, s2, tr, st);
+            if (f_final) memcpy(f_final + (size_t)q * N, f, sizeof(double) * N);
+            if (S1) memcpy(S1 + (size_t)q * N, s1, sizeof(double) * N);
+            if (S2) memcpy(S2 + (size_t)q * N, s2, sizeof(double) * N);
+            if (chi2_final) chi2_final[q] = ora_chi2(p, f);
+            for (int k = 0; k < 4; ++k) loc[k] += st[k];
+        }
+#pragma omp critical
+        for (int k = 0; k < 4; ++k) tot[k] += loc[k];
+        free(f); free(s1); free(s2);
+    }
+    if (stats) for (int k = 0; k < 4; ++k) stats[k] = tot[k];
+    return 0;
+}
+
+int ora_run(const ora_problem *p, int chains, long burn_in, long sweeps, uint64_t seed,
+            uint64_t problem_id, int n_threads, double *f_final, double *S1, double *S2,
+            double *chi2_final, double *trace, int n_traced, long *stats)
+{
+    double *f0 = (double *)malloc(sizeof(double) * (size_t)chains * p->N);
+    ora_initial_f(p, f0);
+    for (int q = 1; q < chains; ++q) memcpy(f0 + (size_t)q * p->N, f0, sizeof(double) * p->N);
+    int rc = ora_run_from(p, chains, f0, 0, burn_in, sweeps, seed, problem_id, n_threads,
+                          f_final, S1, S2, chi2_final, trace, n_traced, stats);
+    free(f0);
+    return rc;
+}
