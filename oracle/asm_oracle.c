@@ -130,13 +130,18 @@ static double ora_right_tail(double a, double b, double u, int *capped)
         double q = (1.0 - u) * qa + u * qb;
         y = -ora_norm_quantile(q) - a;
     } else {
-        /* log space: log Q(a + y) - log Q(a) = log((1-u) + u Q(b)/Q(a)) */
-        double la = ora_log_q(a);
-        double r = isinf(b) ? 0.0 : exp(ora_log_q(b) - la);
-        /* both forms are exact in 1 - u (u is on the 2^-52 grid); each keeps
-         * the relative accuracy of the small quantity in its own regime */
-        double dt = u < 0.5 ? log1p(-u * (1.0 - r)) : log((1.0 - u) + u * r);
+        /* log space: log Q(a + y) - log Q(a) = log((1-u) + u r), r = Q(b)/Q(a).
+         * r is formed from erfcx(b)/erfcx(a) and the exact (b-a)(b+a)/2 so that
+         * 1 - r keeps its relative accuracy on narrow intervals; 1 - u is exact
+         * because u lies on the 2^-52 grid. */
         double exa = ora_erfcx(a / ORA_SQRT2);
+        double r = 0.0, em = -1.0;
+        if (!isinf(b)) {
+            double lr = log(ora_erfcx(b / ORA_SQRT2) / exa) - 0.5 * (b - a) * (b + a);
+            r = exp(lr);
+            em = expm1(lr);
+        }
+        double dt = r < 0.5 ? log((1.0 - u) + u * r) : log1p(u * em);
         y = -dt / a;
         int it;
         for (it = 0; it < 100; ++it) {

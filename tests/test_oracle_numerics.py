@@ -84,7 +84,8 @@ def _exact_std(a, b, u):
 
 INTERVALS = [(-1, 2), (0.5, 3), (5, np.inf), (30, 31), (1000, np.inf), (-np.inf, -7),
              (-40, -39.9), (-400, -300), (-1e-3, 1e-3), (4.9, 5.1), (-3, np.inf), (0, np.inf),
-             (-np.inf, 0), (-np.inf, np.inf), (6, 6.000001), (1e6, np.inf)]
+             (-np.inf, 0), (-np.inf, np.inf), (6, 6.000001), (1e6, np.inf),
+             (1000, 1000 + 1e-7), (-50 - 1e-6, -50), (7, 7.5)]
 US = [2.0**-53, 1e-9, 0.01, 0.37, 0.5, 0.93, 1 - 1e-9, 1 - 2.0**-53]
 
 
