@@ -1,0 +1,337 @@
+"""Benchmark of the GB300 average-spectrum sampler (blocked modes sampling).
+
+Workload: the blocked-modes problem -- fermionic kernel, beta = 20,
+N_tau = 100, N_omega = 400 on a Gaussian-density grid (sigma 3) on [-8, 8],
+levels {global, 8 blocks of 50}, correlated noise 1e-4 exp(-|dtau|/0.5),
+1024 chains, 1000 burn-in + 10^4 sweeps per step.  Synthetic inputs from
+paper_1912_01379_gb300.workloads (seeded).
+
+One step = one asm_sample call over the whole workload (burn-in included) in
+the mixed FP32/FP64 path.  `value` = chain-mode updates per second
+(chains x sweeps x N_omega per step, burn-in included) with the inputs resident
+on the device; `e2e` runs asm_setup from host arrays + asm_sample + asm_average
+(device->host results) per step.  The plain FP64 path and ESS/s of <A(omega)>
+are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1912_01379_gb300 import workloads as W  # noqa: E402
+
+METRIC = "chain-mode updates/s and ESS/s of <A(omega)>: mixed-prec vs plain FP64, 1 GB300"
+UNIT = "chain-mode updates/s"
+WORKLOAD = "blocked_modes_fermionic_b20_Ntau100_Nomega400_gauss3_8x50_1024chains"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--burn", type=int, default=1000)
+    ap.add_argument("--sweeps", type=int, default=10000)
+    ap.add_argument("--chains", type=int, default=1024)
+    ap.add_argument("--fp64-sweeps", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, lrank
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _level_sequence(seed, n_sweeps, n_levels, problem_id=0):
+    """Levels drawn by the sampler (Philox4x64-10 word 0 of ctr {2^64-1, s, 0, p}).
+    numpy's Philox adds one to its counter before each block."""
+    out = np.empty(n_sweeps, dtype=np.int64)
+    key = np.array([seed, 0], dtype=np.uint64)
+    for s in range(n_sweeps):
+        bg = np.random.Philox(key=key, counter=np.array([2**64 - 2, s, 0, problem_id], dtype=np.uint64))
+        w = int(bg.random_raw(1)[0])
+        u = ((w >> 12) + 0.5) * 2.0 ** -52
+        out[s] = min(int(u * n_levels), n_levels - 1)
+    return out
+
+
+def _ops_per_level(p):
+    """Algorithmic FP32 lane operations per chain and sweep at every level:
+    6 per element per move (update FMA, clamp, two bound products, two masked
+    min/max) plus 2 M min(M, n_b) for the block's entry and exit projections."""
+    ops = []
+    for starts in p.levels:
+        ends = list(starts[1:]) + [p.N]
+        tot = 0
+        for s, e in zip(starts, ends):
+            n = int(e - s)
+            tot += 6 * n * n + 2 * p.M * min(p.M, n)
+        ops.append(tot)
+    return np.array(ops, dtype=np.float64)
+
+
+def _peaks():
+    try:
+        with open(PEAKS) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(p, seconds_target=12.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the same workload: chains x sweeps from the same initial state."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    op = O.OracleProblem(p.K, p.G, p.C, p.levels)
+    chains = cores
+    t0 = time.perf_counter()
+    op.run(chains, 0, 2, seed=5, threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    sweeps = int(max(2, min(400, 2 * seconds_target / dt)))
+    t0 = time.perf_counter()
+    op.run(chains, 0, sweeps, seed=6, threads=cores)
+    dt = time.perf_counter() - t0
+    upd = chains * sweeps * p.N
+    return {"value": upd / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{chains} chains x {sweeps} sweeps of the same workload (FP64 oracle, OpenMP over chains)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle is the reference arm for this method."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    p = W.blocked_modes_problem(chains=args.chains)
+    for _ in range(args.warmup):
+        cpu_baseline(p, seconds_target=2.0)
+    vals, secs = [], 0.0
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(p, seconds_target=6.0)
+        vals.append(last["value"])
+        secs += last["seconds"]
+    v = float(np.mean(vals))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"kind": "oracle", "cores": last["cores"], "sample": last["sample"], "value": v,
+                         "unit": UNIT},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_1912_01379_gb300 import asm
+    ws, rank, lrank = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(lrank)
+    dev = torch.cuda.current_device()
+
+    p = W.blocked_modes_problem(chains=args.chains)
+    gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w)
+    chains, burn, sweeps = args.chains, args.burn, args.sweeps
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    seed_base = 1000 + 7919 * rank           # replicas: independent chains per rank
+
+    # warm-up (untimed), full steps
+    for w in range(args.warmup):
+        gp.sample(chains, burn, sweeps if w == args.warmup - 1 else max(sweeps // 10, 64), seed_base + w)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed between steps, CUDA events per step
+    ops_lvl = _ops_per_level(p)
+    clk = ClockSampler(dev)
+    clk.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms, sweep_ms, sweep_launches, other_launches, ops_total = [], 0.0, 0, 0, 0.0
+    ess_min = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        seed = seed_base + 100 + k
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gp.sample(chains, burn, sweeps, seed, timing=True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = gp.status()
+        sweep_ms += st["sweep_kernel_ms"]
+        sweep_launches += st["timed_launches"]
+        other_launches += st["other_launches"]
+        r = gp.average()
+        ess_min.append(float(np.nanmin(r["ess"])))
+        lv = _level_sequence(seed, burn + sweeps, len(p.levels))
+        ops_total += chains * float(np.sum(ops_lvl[lv]))
+    torch.cuda.synchronize()
+    t_local = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    clocks = clk.stop()
+    updates_per_step = chains * (burn + sweeps) * p.N
+    value = ws * args.steps * updates_per_step / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+    ess_per_s = float(np.mean(ess_min)) / (ms_per_step / 1e3)
+
+    # dominant kernel roofline: FP32 lane operations (ALU-bound path)
+    peaks, src = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12    # T lane-op/s
+    achieved = ops_total / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
+
+    # plain FP64 path, same workload, shorter run (a rate)
+    fp64 = None
+    if args.fp64_sweeps > 0:
+        f64s = args.fp64_sweeps
+        gp.sample(chains, 0, 64, seed_base + 999, precision=asm.ASM_FP64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gp.sample(chains, f64s // 10, f64s, seed_base + 1000, precision=asm.ASM_FP64)
+        e1.record(stream)
+        e1.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        r64 = gp.average()
+        upd64 = chains * (f64s + f64s // 10) * p.N
+        fp64 = {"updates_per_s": upd64 / t64, "ess_per_s": float(np.nanmin(r64["ess"])) / t64,
+                "sweeps": f64s, "burn_in": f64s // 10}
+
+    # end to end through the C ABI from host buffers
+    e2e = None
+    if not args.no_e2e:
+        h2d = sum(a.nbytes for a in (p.K, p.G, p.C, p.w)) + sum(np.asarray(l).nbytes for l in p.levels)
+        d2h = 4 * p.N * 8
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(max(1, min(args.steps, 2))):
+            q = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w)
+            q.sample(chains, burn, sweeps, seed_base + 200 + k)
+            q.average()
+            del q
+        torch.cuda.synchronize()
+        nst = max(1, min(args.steps, 2))
+        te = (time.perf_counter() - t0) / nst
+        e2e = {"value": ws * updates_per_step / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": nst}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "chains_per_gpu": chains, "burn_in": burn, "sweeps": sweeps,
+                       "N_omega": p.N, "N_tau": p.M, "levels": "global + 8x50", "precision": "mixed FP32/FP64",
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+            "ess_per_s": ess_per_s,
+            "fp64": fp64,
+            "speedup_vs_fp64": (value / ws) / fp64["updates_per_s"] if fp64 else None,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-op/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({src} sm_max_mhz)",
+                         "kernel": "sweep_kernel<float>", "avg_launch_ms": sweep_ms / max(sweep_launches, 1)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(sweep_launches + other_launches + args.steps),
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

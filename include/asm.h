@@ -1,0 +1,155 @@
+/*
+ * asm.h -- C ABI of the GB300 sampler for the average spectrum method with
+ * blocked modes sampling (K. Ghanem and E. Koch, "The Average Spectrum Method
+ * for Analytic Continuation: Efficient Blocked Modes Sampling and Dependence on
+ * Discretization Grid", arXiv:1912.01379).
+ *
+ * The library estimates the functional average of Eq. PI, discretised as
+ * Eq. MCint: the mean of non-negative vectors fbar (fbar_n = A(omega_n) w_n,
+ * Sec. V.B, Eq. Riemann) under the weight exp(-chi^2/2) of Eq. chi2, by Gibbs
+ * moves along the right singular vectors of the whitened kernel restricted to
+ * the blocks of a randomly chosen level (Sec. IV.B modes, IV.C blocked modes).
+ *
+ * Conventions for every call:
+ *  - Return value: ASM_OK (0) or a negative ASM_ERR_* code; no exception or
+ *    signal crosses this boundary.  asm_error_string() names the code.
+ *  - Host arrays are plain C arrays owned by the caller; the library copies
+ *    what it keeps during the call.  Matrices are row-major.
+ *  - Device memory the caller passes (the workspace) stays owned by the caller
+ *    and must stay allocated while the handle uses it.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  asm_sample is asynchronous on it; the result calls synchronise.
+ *  - Handles are not thread-safe: one host thread at a time per handle.
+ *  - All compute runs on the current CUDA device; there is no CPU fallback.
+ */
+#ifndef ASM_GB300_H
+#define ASM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ASM_OK = 0,
+    ASM_ERR_SHAPE = -1,      /* sizes or block partition inconsistent */
+    ASM_ERR_NOT_SPD = -2,    /* covariance not symmetric positive definite */
+    ASM_ERR_NONFINITE = -3,  /* NaN or Inf in an input */
+    ASM_ERR_IMPROPER = -4,   /* a zero mode along which f >= 0 gives no bound */
+    ASM_ERR_CUDA = -5,       /* a CUDA, cuBLAS or cuSOLVER call failed */
+    ASM_ERR_STATE = -6,      /* call out of order (e.g. average before sample) */
+    ASM_ERR_ARG = -7,        /* NULL or out-of-range argument */
+    ASM_ERR_WORKSPACE = -8,  /* workspace missing, too small or misaligned */
+    ASM_ERR_TOO_LARGE = -9   /* a block or level exceeds a compiled limit */
+};
+
+enum { ASM_FP64 = 0, ASM_MIXED = 1 };   /* precision of asm_sample */
+
+/* asm_sample flags */
+#define ASM_SAMPLE_CONTINUE 1u   /* keep the chains of the previous call and go on */
+#define ASM_SAMPLE_TIMING 2u     /* record CUDA events around every sweep-kernel launch */
+
+typedef struct asm_problem asm_problem;  /* opaque, library-owned */
+
+/* Problem description (Sec. II, Eq. likelihood and Eq. matrixeq; Sec. IV.C).
+ *  M, N          number of data points (N_tau) and grid points (N_omega).
+ *  K             M x N kernel acting on fbar: data mean = K fbar.
+ *  G             M data (the mean gbar).
+ *  C             M x M covariance of the data mean (symmetric positive definite).
+ *  w             N Riemann weights (A = fbar / w); NULL means all ones.
+ *  n_levels      number of partition levels (>= 1).
+ *  level_nblocks blocks per level.
+ *  block_start   concatenated start indices of the blocks of every level; each
+ *                level starts at 0, starts increase, a block ends where the next
+ *                one starts (the last one at N).  A level with one block is modes
+ *                sampling; one-point blocks are components sampling.
+ *  Kt, gt, d, V, U  optional given factors.  If all five are non-NULL, the
+ *                library skips whitening and SVDs and uses them instead:
+ *                Kt (M x N whitened kernel), gt (M whitened data) and, block
+ *                after block in level order, d (n_b singular values, 0 marks a
+ *                zero mode), V (n_b x n_b, mode-major: V[j*n_b+i] = component i
+ *                of mode j) and U (min(M,n_b) x M, mode-major).  K, G, C are then
+ *                unused.  This reproduces another implementation's modes.
+ *  flags         reserved, 0. */
+typedef struct {
+    int M, N;
+    const double *K;
+    const double *G;
+    const double *C;
+    const double *w;
+    int n_levels;
+    const int *level_nblocks;
+    const int *block_start;
+    const double *Kt, *gt, *d, *V, *U;
+    uint32_t flags;
+} asm_desc;
+
+/* Counters of the last asm_sample run (asm_status). */
+typedef struct {
+    int64_t chains, sweeps_done, kept_sweeps, precision;
+    int64_t degenerate_moves;   /* interval of zero width: step 0 */
+    int64_t zero_mode_moves;    /* flat draws along zero modes */
+    int64_t tail_capped;        /* far-tail inverse-CDF solves that hit the cap */
+    int64_t nonfinite_moves;    /* steps that came out NaN/Inf (then set to 0) */
+    double max_resync_drift;    /* max |chi2_tracked - chi2_exact| / chi2_exact at refreshes */
+    int64_t sweep_launches;     /* sweep-kernel launches since set-up of the chains */
+    int64_t other_launches;     /* initial-state, refresh and reduction launches */
+    int64_t timed_launches;     /* sweep launches timed with ASM_SAMPLE_TIMING */
+    double sweep_kernel_ms;     /* summed event-timed duration of those launches */
+} asm_stats;
+
+/* Set-up (Sec. IV: whitening C^{-1} = T^T T by Cholesky, K~ = T K, g~ = T G;
+ * Sec. IV.B-C: SVD K~_b = U_b D_b V_b^T of every block of every level, in FP64
+ * on the device).  Singular vectors get the sign that makes the largest
+ * |component| of each V_j positive; d <= d_1 max(M,n_b) 2^-52 counts as a zero
+ * mode.  On success *out receives a new handle (free with asm_destroy). */
+int asm_setup(const asm_desc *d, asm_problem **out);
+
+/* Bytes of device workspace asm_sample needs for `chains` chains at
+ * `precision` (ASM_FP64 or ASM_MIXED); 0 for invalid arguments. */
+size_t asm_workspace_bytes(const asm_problem *p, int chains, int precision);
+
+/* Run burn_in + sweeps sweeps of `chains` independent chains (Sec. IV.C: every
+ * sweep draws one level at random and moves every mode of every block of it
+ * once, blocks left to right, modes in index order).  Each move draws the step
+ * along its mode from the exact 1-D conditional, a Gaussian truncated to the
+ * interval of Eq. modeLimits (flat for zero modes), by the inverse CDF of one
+ * Philox4x64-10 uniform keyed by (seed, problem 0, chain, sweep, move).
+ * Sweeps after burn-in are accumulated into FP64 sums of fbar and fbar^2.
+ * precision: ASM_FP64 runs the chain state in FP64; ASM_MIXED runs it in FP32
+ * with FP64 accumulators and an FP64 residual refresh every 64 sweeps.
+ * flags: ASM_SAMPLE_CONTINUE continues the chains of the previous call on the
+ * same workspace (same chains, seed and precision) without resetting the sums;
+ * otherwise chains start from the flat default-model scale fit.
+ * ASM_SAMPLE_TIMING records a CUDA event pair on `stream` around every sweep
+ * launch; asm_status reports their summed duration.
+ * d_workspace: device pointer, 256-byte aligned, >= asm_workspace_bytes(). */
+int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t seed,
+               int precision, uint32_t flags, void *d_workspace, size_t workspace_bytes,
+               void *stream);
+
+/* Results of the last asm_sample (synchronises).  Per grid point (N values,
+ * any pointer may be NULL): mean_A = <fbar>/w, sem_A its standard error from
+ * the spread of the independent chain means, ess = posterior variance of fbar
+ * over sem^2, mean_fbar = <fbar>. */
+int asm_average(asm_problem *p, double *mean_A, double *sem_A, double *ess, double *mean_fbar);
+
+/* Current chain states (synchronises): f (chains x N, FP64 copy of fbar) and
+ * chi2 (chains) = |r~|^2 of the residual the sampler tracks; either may be NULL. */
+int asm_chain_state(asm_problem *p, double *f, double *chi2);
+
+/* Counters of the last asm_sample (synchronises). */
+int asm_status(asm_problem *p, asm_stats *out);
+
+/* Free the handle and its device memory (not the caller's workspace). */
+void asm_destroy(asm_problem *p);
+
+/* Static string naming an ASM_* code. */
+const char *asm_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

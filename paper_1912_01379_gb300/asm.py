@@ -1,0 +1,190 @@
+"""Thin Python binding of the C ABI in include/asm.h (ctypes).
+
+Argument marshalling only: every step of the sampling path runs in the CUDA
+library libasm_gb300.so.  PyTorch supplies the device workspace and the
+stream.  There is no CPU fallback: if the library or a GPU is missing, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ASM_OK = 0
+ASM_FP64 = 0
+ASM_MIXED = 1
+ASM_SAMPLE_CONTINUE = 1
+ASM_SAMPLE_TIMING = 2
+
+_dp = ct.POINTER(ct.c_double)
+_ip = ct.POINTER(ct.c_int)
+
+
+class asm_desc(ct.Structure):
+    _fields_ = [("M", ct.c_int), ("N", ct.c_int),
+                ("K", _dp), ("G", _dp), ("C", _dp), ("w", _dp),
+                ("n_levels", ct.c_int), ("level_nblocks", _ip), ("block_start", _ip),
+                ("Kt", _dp), ("gt", _dp), ("d", _dp), ("V", _dp), ("U", _dp),
+                ("flags", ct.c_uint32)]
+
+
+class asm_stats(ct.Structure):
+    _fields_ = [("chains", ct.c_int64), ("sweeps_done", ct.c_int64), ("kept_sweeps", ct.c_int64),
+                ("precision", ct.c_int64), ("degenerate_moves", ct.c_int64),
+                ("zero_mode_moves", ct.c_int64), ("tail_capped", ct.c_int64),
+                ("nonfinite_moves", ct.c_int64), ("max_resync_drift", ct.c_double),
+                ("sweep_launches", ct.c_int64), ("other_launches", ct.c_int64),
+                ("timed_launches", ct.c_int64), ("sweep_kernel_ms", ct.c_double)]
+
+
+EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",
+           "asm_status", "asm_destroy", "asm_error_string"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libasm_gb300.so (building it in-tree first if asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path}")
+        _build.build()
+    L = ct.CDLL(path)
+    L.asm_setup.argtypes = [ct.POINTER(asm_desc), ct.POINTER(ct.c_void_p)]
+    L.asm_setup.restype = ct.c_int
+    L.asm_workspace_bytes.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
+    L.asm_workspace_bytes.restype = ct.c_size_t
+    L.asm_sample.argtypes = [ct.c_void_p, ct.c_int, ct.c_long, ct.c_long, ct.c_uint64, ct.c_int,
+                             ct.c_uint32, ct.c_void_p, ct.c_size_t, ct.c_void_p]
+    L.asm_sample.restype = ct.c_int
+    L.asm_average.argtypes = [ct.c_void_p, _dp, _dp, _dp, _dp]
+    L.asm_average.restype = ct.c_int
+    L.asm_chain_state.argtypes = [ct.c_void_p, _dp, _dp]
+    L.asm_chain_state.restype = ct.c_int
+    L.asm_status.argtypes = [ct.c_void_p, ct.POINTER(asm_stats)]
+    L.asm_status.restype = ct.c_int
+    L.asm_destroy.argtypes = [ct.c_void_p]
+    L.asm_destroy.restype = None
+    L.asm_error_string.argtypes = [ct.c_int]
+    L.asm_error_string.restype = ct.c_char_p
+    _lib = L
+    return L
+
+
+class ASMError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {load().asm_error_string(code).decode()} ({code})")
+
+
+def _check(code, where):
+    if code != ASM_OK:
+        raise ASMError(code, where)
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _require_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the average-spectrum sampler runs on a CUDA GPU only (no CPU fallback)")
+    return torch
+
+
+class Problem:
+    """A set-up problem: owns the library handle and a torch workspace.
+
+    K (M x N, acting on fbar), G (M), C (M x M) and the levels (list of arrays
+    of block starts) follow Sec. II and IV of the paper; w are the Riemann
+    weights (A = fbar / w).  `factors` (optional) is an object with Kt, gt, d,
+    V, U arrays in the layout of asm_desc to use given singular vectors."""
+
+    def __init__(self, K, G, C, levels, w=None, factors=None):
+        L = load()
+        self._keep = []
+        K = np.ascontiguousarray(K, dtype=np.float64)
+        self.M, self.N = K.shape
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        C = np.ascontiguousarray(C, dtype=np.float64)
+        self.w = np.ones(self.N) if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        self.levels = [np.asarray(l, dtype=np.int32) for l in levels]
+        nb = np.array([len(l) for l in self.levels], dtype=np.int32)
+        bs = np.concatenate(self.levels).astype(np.int32)
+        d = asm_desc()
+        d.M, d.N = self.M, self.N
+        d.K, d.G, d.C, d.w = _dptr(K), _dptr(G), _dptr(C), _dptr(self.w)
+        d.n_levels = len(self.levels)
+        d.level_nblocks = nb.ctypes.data_as(_ip)
+        d.block_start = bs.ctypes.data_as(_ip)
+        self._keep += [K, G, C, nb, bs]
+        if factors is not None:
+            arrs = [np.ascontiguousarray(getattr(factors, k), dtype=np.float64) for k in ("Kt", "gt", "d", "V", "U")]
+            self._keep += arrs
+            d.Kt, d.gt, d.d, d.V, d.U = (_dptr(a) for a in arrs)
+        h = ct.c_void_p()
+        _check(L.asm_setup(ct.byref(d), ct.byref(h)), "asm_setup")
+        self._h = h
+        self._ws = None
+        self.chains = 0
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.asm_destroy(self._h)
+            self._h = None
+
+    def workspace_bytes(self, chains, precision=ASM_MIXED):
+        return int(load().asm_workspace_bytes(self._h, chains, precision))
+
+    def sample(self, chains, burn_in, sweeps, seed, precision=ASM_MIXED, cont=False, stream=None,
+               workspace=None, timing=False):
+        """asm_sample on a torch workspace (allocated here unless given) and the
+        current torch stream (or `stream`)."""
+        torch = _require_cuda()
+        need = self.workspace_bytes(chains, precision)
+        if need == 0:
+            raise ASMError(-7, "asm_workspace_bytes")
+        if workspace is None:
+            if self._ws is None or self._ws.numel() < need or self._ws.device != torch.device("cuda", torch.cuda.current_device()):
+                self._ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+            workspace = self._ws
+        else:
+            self._ws = workspace
+        s = stream if stream is not None else torch.cuda.current_stream()
+        flags = (ASM_SAMPLE_CONTINUE if cont else 0) | (ASM_SAMPLE_TIMING if timing else 0)
+        _check(load().asm_sample(self._h, chains, burn_in, sweeps, ct.c_uint64(seed), precision, flags,
+                                 ct.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                 ct.c_void_p(s.cuda_stream)), "asm_sample")
+        self.chains = chains
+
+    def average(self):
+        N = self.N
+        mean_A, sem_A, ess, mean_f = (np.zeros(N) for _ in range(4))
+        _check(load().asm_average(self._h, _dptr(mean_A), _dptr(sem_A), _dptr(ess), _dptr(mean_f)),
+               "asm_average")
+        return {"mean_A": mean_A, "sem_A": sem_A, "ess": ess, "mean_fbar": mean_f,
+                "sem_fbar": sem_A * self.w}
+
+    def chain_state(self):
+        f = np.zeros((self.chains, self.N))
+        chi2 = np.zeros(self.chains)
+        _check(load().asm_chain_state(self._h, _dptr(f), _dptr(chi2)), "asm_chain_state")
+        return f, chi2
+
+    def status(self):
+        st = asm_stats()
+        _check(load().asm_status(self._h, ct.byref(st)), "asm_status")
+        return {k: getattr(st, k) for k, _ in asm_stats._fields_}

@@ -1,0 +1,70 @@
+// asm_internal.h -- types shared by the host library and the sweep kernels.
+// Not part of the public ABI (include/asm.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace asmgb {
+
+// Rows of every block's mode data are padded to a multiple of this many
+// elements so that any team size S <= 32 with 16-byte vectors stays in the row.
+constexpr int kRowAlign = 128;
+// Residual refresh period of the sweep loop (sweeps).
+constexpr int kRefreshPeriod = 64;
+
+// One block of one level, as the device sees it.  Offsets are in elements of
+// the precision-specific arrays.
+struct BlockDesc {
+    int start;       // first grid point of the block
+    int n;           // block width n_b
+    int np;          // modes with a U column: min(M, n_b)
+    int rs;          // row stride of V/Rlo/Rhi rows (multiple of kRowAlign)
+    long long offV;  // V/Rlo/Rhi: n rows (Rlo/Rhi: n + 1 rows, the last all-NaN)
+    long long offR;  // Rlo/Rhi base
+    long long offd;  // d, invd: n values
+    long long offU;  // Ut: np x M (mode-major); Um: M x np (grid-major)
+};
+
+// Device-side problem data in one precision T.
+template <class T>
+struct ProblemData {
+    const T *V, *Rlo, *Rhi;  // mode rows
+    const T *d, *invd;       // singular values and their reciprocals (0 for zero modes)
+    const T *Ut, *Um;        // U in two layouts
+};
+
+struct Counters {            // device counters, first bytes of the workspace
+    unsigned long long degenerate, zero_mode, tail_capped, nonfinite;
+    unsigned long long drift_bits;   // max relative chi2 drift, as ordered bits of a double
+    unsigned long long pad[3];
+};
+
+template <class T>
+struct SweepParams {
+    int M, N, S;                      // S: lanes per chain (power of two, <= 32)
+    int n_levels;
+    const int *level_first;           // first block index of each level
+    const int *level_nblocks;
+    const BlockDesc *blocks;
+    ProblemData<T> pd;
+    T *F; int ldF;                    // chain states, chains x ldF
+    T *R; int ldR;                    // tracked residuals, chains x ldR
+    double *S1, *S2;                  // sums of f and f^2, chains x N
+    int chains;
+    long long sweep0, nsweeps, burn_in;
+    unsigned long long seed, problem_id;
+    Counters *counters;
+    int cpad;                         // shared-memory stride of the c/w buffers (>= max np)
+    int mpad;                         // shared-memory stride of the residual (>= M)
+};
+
+// Launchers (asm_sweep_f32.cu / asm_sweep_f64.cu).  kv: 16-byte vectors per lane.
+cudaError_t launch_sweeps_f32(const SweepParams<float> &p, int kv, int warps_per_cta, cudaStream_t s);
+cudaError_t launch_sweeps_f64(const SweepParams<double> &p, int kv, int warps_per_cta, cudaStream_t s);
+// Largest supported kv per precision.
+constexpr int kMaxKvF32 = 16;   // 64 floats per lane
+constexpr int kMaxKvF64 = 32;   // 64 doubles per lane
+
+}  // namespace asmgb

@@ -1,0 +1,791 @@
+// asm_lib.cu -- C ABI (include/asm.h) of the GB300 average-spectrum sampler:
+// set-up (whitening and block SVDs in FP64 on the device), the sweep loop with
+// the periodic FP64 residual refresh, and the result reductions.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <vector>
+
+#include "../../include/asm.h"
+#include "asm_internal.h"
+
+using namespace asmgb;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// small device kernels: initial state, residual refresh, result reduction
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void init_kernel(T *F, int ldF, int N, double f0, double *S1, double *S2, int chains)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)chains * ldF;
+    if (i < tot) {
+        const int n = (int)(i % ldF);
+        F[i] = n < N ? (T)f0 : T(0);
+    }
+    if (i < (long long)chains * N) {
+        S1[i] = 0.0;
+        S2[i] = 0.0;
+    }
+}
+
+// r~ = g~ - K~ f in FP64 for every chain (one CTA per chain); chi2 = |r~|^2.
+// Records the largest relative change of chi2 against the tracked residual.
+template <class T>
+__global__ void refresh_kernel(int M, int N, const double *__restrict__ KtT, const double *__restrict__ gt,
+                               const T *__restrict__ F, int ldF, T *R, int ldR, double *chi2,
+                               Counters *cnt, int track_drift)
+{
+    extern __shared__ double fs[];
+    __shared__ double red_old[32], red_new[32];
+    const int q = blockIdx.x;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) fs[n] = (double)F[(size_t)q * ldF + n];
+    __syncthreads();
+    double so = 0.0, sn = 0.0;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        double a = gt[m];
+        for (int n = 0; n < N; ++n) a -= KtT[(size_t)n * M + m] * fs[n];
+        const double old = (double)R[(size_t)q * ldR + m];
+        so += old * old;
+        sn += a * a;
+        R[(size_t)q * ldR + m] = (T)a;
+    }
+    for (int off = 16; off; off >>= 1) {
+        so += __shfl_xor_sync(0xffffffffu, so, off);
+        sn += __shfl_xor_sync(0xffffffffu, sn, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red_old[threadIdx.x >> 5] = so;
+        red_new[threadIdx.x >> 5] = sn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red_old[w]; b += red_new[w]; }
+        if (chi2) chi2[q] = b;
+        if (track_drift) {
+            const double drift = fabs(a - b) / fmax(b, 1e-300);
+            atomicMax(&cnt->drift_bits, (unsigned long long)__double_as_longlong(drift));
+        }
+    }
+}
+
+// Per grid point: mean over chains and kept sweeps, the spread of the chain
+// means (two passes) and the second moment.
+__global__ void reduce_kernel(const double *S1, const double *S2, int chains, int N, double kept,
+                              double *mean, double *semsq, double *m2)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < chains; ++q) {
+        a += S1[(size_t)q * N + n];
+        b += S2[(size_t)q * N + n];
+    }
+    const double mu = a / (chains * kept);
+    double v = 0.0;
+    for (int q = 0; q < chains; ++q) {
+        const double d = S1[(size_t)q * N + n] / kept - mu;
+        v += d * d;
+    }
+    mean[n] = mu;
+    semsq[n] = chains > 1 ? v / ((double)(chains - 1) * chains) : NAN;
+    m2[n] = b / (chains * kept);
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+int round_up_int(int x, int a) { return (x + a - 1) / a * a; }
+
+struct WsLayout {
+    size_t counters, F, R, S1, S2, chi2, total;
+    int ldF, ldR;
+};
+
+}  // namespace
+
+// device buffers of one precision
+struct PrecBuffers {
+    void *V = nullptr, *Rlo = nullptr, *Rhi = nullptr, *d = nullptr, *invd = nullptr, *Ut = nullptr,
+         *Um = nullptr;
+};
+
+struct asm_problem {
+    int M = 0, N = 0, n_levels = 0, n_blocks = 0;
+    std::vector<int> level_nblocks, level_first;
+    std::vector<BlockDesc> blocks;
+    std::vector<double> w;
+    double f0 = 0.0;
+    int max_nb = 0, max_np = 0;
+    long long totV = 0, totR = 0, totd = 0, totU = 0;
+    // device
+    int *d_level_first = nullptr, *d_level_nblocks = nullptr;
+    BlockDesc *d_blocks = nullptr;
+    double *d_KtT = nullptr, *d_gt = nullptr;
+    PrecBuffers b64, b32;
+    // run state
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int chains = 0, precision = -1, team = 32;
+    long long sweeps_done = 0, kept = 0;
+    unsigned long long seed = 0;
+    cudaStream_t stream = nullptr;
+    bool have_run = false;
+    // launch bookkeeping
+    long long sweep_launches = 0, other_launches = 0, timed_launches = 0;
+    double timed_ms = 0.0;
+    std::vector<cudaEvent_t> ev_pool;     // pairs (start, stop), reused
+    size_t ev_used = 0;                   // events recorded and not yet read
+    bool timing = false;
+};
+
+namespace {
+
+WsLayout ws_layout(const asm_problem *p, int chains, int precision)
+{
+    WsLayout L{};
+    const size_t es = precision == ASM_FP64 ? 8 : 4;
+    L.ldF = round_up_int(p->N, 4);
+    L.ldR = round_up_int(p->M, 4);
+    size_t off = 0;
+    L.counters = off; off = align_up(off + sizeof(Counters), 256);
+    L.F = off; off = align_up(off + (size_t)chains * L.ldF * es, 256);
+    L.R = off; off = align_up(off + (size_t)chains * L.ldR * es, 256);
+    L.S1 = off; off = align_up(off + (size_t)chains * p->N * 8, 256);
+    L.S2 = off; off = align_up(off + (size_t)chains * p->N * 8, 256);
+    L.chi2 = off; off = align_up(off + (size_t)chains * 8, 256);
+    L.total = off;
+    return L;
+}
+
+template <class T>
+int upload(void **dst, const std::vector<T> &src)
+{
+    if (cudaMalloc(dst, std::max<size_t>(src.size(), 1) * sizeof(T)) != cudaSuccess) return ASM_ERR_CUDA;
+    if (!src.empty() &&
+        cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    return ASM_OK;
+}
+
+void free_prec(PrecBuffers &b)
+{
+    void *ptrs[] = {b.V, b.Rlo, b.Rhi, b.d, b.invd, b.Ut, b.Um};
+    for (void *x : ptrs)
+        if (x) cudaFree(x);
+    b = PrecBuffers{};
+}
+
+// Per-block factors in host FP64 (mode-major), produced either by cuSOLVER or
+// given by the caller.
+struct HostFactors {
+    std::vector<double> Kt, gt;            // M x N row-major, M
+    std::vector<std::vector<double>> d;    // per block, n
+    std::vector<std::vector<double>> V;    // per block, n x n mode-major
+    std::vector<std::vector<double>> U;    // per block, np x M mode-major
+};
+
+#define CK_CUDA(x) do { if ((x) != cudaSuccess) { rc = ASM_ERR_CUDA; goto done; } } while (0)
+#define CK_CUBLAS(x) do { if ((x) != CUBLAS_STATUS_SUCCESS) { rc = ASM_ERR_CUDA; goto done; } } while (0)
+#define CK_SOLVER(x) do { if ((x) != CUSOLVER_STATUS_SUCCESS) { rc = ASM_ERR_CUDA; goto done; } } while (0)
+
+// Whitening (C = L L^T, K~ = L^{-1} K, g~ = L^{-1} G) and the SVD of every block,
+// all in FP64 on the device (cuSOLVER potrf / gesvd, cuBLAS trsm / trsv).
+int device_factorize(const asm_desc *ds, const asm_problem *p, HostFactors &hf)
+{
+    const int M = ds->M, N = ds->N;
+    int rc = ASM_OK;
+    cusolverDnHandle_t sh = nullptr;
+    cublasHandle_t bh = nullptr;
+    double *dC = nullptr, *dK = nullptr, *dG = nullptr, *dA = nullptr, *dS = nullptr, *dU = nullptr,
+           *dVT = nullptr, *dwork = nullptr, *drwork = nullptr;
+    int *dinfo = nullptr;
+    int info = 0, lwork = 0;
+    const double one = 1.0;
+    std::vector<double> A, S, Uh, VTh;
+
+    CK_SOLVER(cusolverDnCreate(&sh));
+    CK_CUBLAS(cublasCreate(&bh));
+    CK_CUDA(cudaMalloc(&dC, sizeof(double) * M * M));
+    CK_CUDA(cudaMalloc(&dK, sizeof(double) * M * N));
+    CK_CUDA(cudaMalloc(&dG, sizeof(double) * M));
+    CK_CUDA(cudaMalloc(&dinfo, sizeof(int)));
+    CK_CUDA(cudaMemcpy(dC, ds->C, sizeof(double) * M * M, cudaMemcpyHostToDevice));
+    CK_CUDA(cudaMemcpy(dK, ds->K, sizeof(double) * M * N, cudaMemcpyHostToDevice));
+    CK_CUDA(cudaMemcpy(dG, ds->G, sizeof(double) * M, cudaMemcpyHostToDevice));
+    // Cholesky of the (symmetric) covariance: row-major and column-major agree
+    CK_SOLVER(cusolverDnDpotrf_bufferSize(sh, CUBLAS_FILL_MODE_LOWER, M, dC, M, &lwork));
+    CK_CUDA(cudaMalloc(&dwork, sizeof(double) * std::max(lwork, 1)));
+    CK_SOLVER(cusolverDnDpotrf(sh, CUBLAS_FILL_MODE_LOWER, M, dC, M, dwork, lwork, dinfo));
+    CK_CUDA(cudaMemcpy(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost));
+    if (info != 0) { rc = ASM_ERR_NOT_SPD; goto done; }
+    cudaFree(dwork); dwork = nullptr;
+    // K row-major M x N is K^T column-major (N x M): solve X L^T = K^T, X = K~^T
+    CK_CUBLAS(cublasDtrsm(bh, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT,
+                          N, M, &one, dC, M, dK, N));
+    CK_CUBLAS(cublasDtrsv(bh, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, M, dC, M, dG, 1));
+    hf.Kt.resize((size_t)M * N);
+    hf.gt.resize(M);
+    CK_CUDA(cudaMemcpy(hf.Kt.data(), dK, sizeof(double) * M * N, cudaMemcpyDeviceToHost));
+    CK_CUDA(cudaMemcpy(hf.gt.data(), dG, sizeof(double) * M, cudaMemcpyDeviceToHost));
+
+    hf.d.resize(p->n_blocks);
+    hf.V.resize(p->n_blocks);
+    hf.U.resize(p->n_blocks);
+    for (int b = 0; b < p->n_blocks; ++b) {
+        const int s0 = p->blocks[b].start, n = p->blocks[b].n, np = std::min(M, n);
+        const bool tall = M >= n;             // gesvd wants rows >= columns
+        const int rm = tall ? M : n, cn = tall ? n : M;
+        A.assign((size_t)rm * cn, 0.0);
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double x = hf.Kt[(size_t)i * N + s0 + j];
+                if (tall) A[i + (size_t)j * M] = x;     // A (M x n), column-major
+                else A[j + (size_t)i * n] = x;          // A^T (n x M), column-major
+            }
+        CK_CUDA(cudaMalloc(&dA, sizeof(double) * rm * cn));
+        CK_CUDA(cudaMalloc(&dS, sizeof(double) * cn));
+        CK_CUDA(cudaMalloc(&dU, sizeof(double) * rm * (tall ? cn : rm)));
+        CK_CUDA(cudaMalloc(&dVT, sizeof(double) * cn * cn));
+        CK_CUDA(cudaMalloc(&drwork, sizeof(double) * std::max(cn, 2)));
+        CK_CUDA(cudaMemcpy(dA, A.data(), sizeof(double) * rm * cn, cudaMemcpyHostToDevice));
+        CK_SOLVER(cusolverDnDgesvd_bufferSize(sh, rm, cn, &lwork));
+        CK_CUDA(cudaMalloc(&dwork, sizeof(double) * std::max(lwork, 1)));
+        CK_SOLVER(cusolverDnDgesvd(sh, tall ? 'S' : 'A', 'A', rm, cn, dA, rm, dS, dU, rm, dVT, cn, dwork,
+                                   lwork, drwork, dinfo));
+        CK_CUDA(cudaMemcpy(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost));
+        if (info != 0) { rc = ASM_ERR_CUDA; goto done; }
+        S.resize(cn);
+        Uh.resize((size_t)rm * (tall ? cn : rm));
+        VTh.resize((size_t)cn * cn);
+        CK_CUDA(cudaMemcpy(S.data(), dS, sizeof(double) * cn, cudaMemcpyDeviceToHost));
+        CK_CUDA(cudaMemcpy(Uh.data(), dU, sizeof(double) * Uh.size(), cudaMemcpyDeviceToHost));
+        CK_CUDA(cudaMemcpy(VTh.data(), dVT, sizeof(double) * VTh.size(), cudaMemcpyDeviceToHost));
+        cudaFree(dA); cudaFree(dS); cudaFree(dU); cudaFree(dVT); cudaFree(dwork); cudaFree(drwork);
+        dA = dS = dU = dVT = dwork = drwork = nullptr;
+
+        std::vector<double> &d = hf.d[b], &V = hf.V[b], &U = hf.U[b];
+        d.assign(n, 0.0);
+        V.assign((size_t)n * n, 0.0);
+        U.assign((size_t)np * M, 0.0);
+        for (int j = 0; j < n; ++j) {
+            for (int i = 0; i < n; ++i)
+                V[(size_t)j * n + i] = tall ? VTh[j + (size_t)i * n] : Uh[i + (size_t)j * n];
+            if (j < np) {
+                d[j] = S[j];
+                for (int m = 0; m < M; ++m) U[(size_t)j * M + m] = tall ? Uh[m + (size_t)j * M] : VTh[j + (size_t)m * M];
+            }
+        }
+        // sign: the largest |component| of every V_j is positive (lowest index on ties)
+        const double thr = (np > 0 ? d[0] : 0.0) * (double)std::max(M, n) * 0x1p-52;
+        for (int j = 0; j < n; ++j) {
+            double *v = &V[(size_t)j * n];
+            int imax = 0;
+            for (int i = 1; i < n; ++i)
+                if (std::fabs(v[i]) > std::fabs(v[imax])) imax = i;
+            if (v[imax] < 0.0) {
+                for (int i = 0; i < n; ++i) v[i] = -v[i];
+                if (j < np)
+                    for (int m = 0; m < M; ++m) U[(size_t)j * M + m] = -U[(size_t)j * M + m];
+            }
+            if (j < np && !(d[j] > thr)) {
+                d[j] = 0.0;
+                for (int m = 0; m < M; ++m) U[(size_t)j * M + m] = 0.0;
+            }
+        }
+    }
+done:
+    if (dC) cudaFree(dC);
+    if (dK) cudaFree(dK);
+    if (dG) cudaFree(dG);
+    if (dA) cudaFree(dA);
+    if (dS) cudaFree(dS);
+    if (dU) cudaFree(dU);
+    if (dVT) cudaFree(dVT);
+    if (dwork) cudaFree(dwork);
+    if (drwork) cudaFree(drwork);
+    if (dinfo) cudaFree(dinfo);
+    if (bh) cublasDestroy(bh);
+    if (sh) cusolverDnDestroy(sh);
+    return rc;
+}
+
+// Host-side mode rows for one precision, then upload.
+template <class T>
+int build_precision(asm_problem *p, const HostFactors &hf, PrecBuffers &out)
+{
+    const int M = p->M;
+    const T nan = std::numeric_limits<T>::quiet_NaN();
+    std::vector<T> V(p->totV, T(0)), Rlo(p->totR, nan), Rhi(p->totR, nan), d(p->totd, T(0)),
+        invd(p->totd, T(0)), Ut(std::max<long long>(p->totU, 1), T(0)), Um(std::max<long long>(p->totU, 1), T(0));
+    for (int b = 0; b < p->n_blocks; ++b) {
+        const BlockDesc &B = p->blocks[b];
+        const std::vector<double> &hd = hf.d[b], &hV = hf.V[b], &hU = hf.U[b];
+        for (int j = 0; j < B.n; ++j) {
+            const double *v = &hV[(size_t)j * B.n];
+            double vmax = 0.0;
+            for (int i = 0; i < B.n; ++i) vmax = std::max(vmax, std::fabs(v[i]));
+            for (int i = 0; i < B.n; ++i) {
+                V[B.offV + (size_t)j * B.rs + i] = (T)v[i];
+                if (std::fabs(v[i]) < 0x1p-40 * vmax) continue;   // left out of the bounds
+                const double r = -1.0 / v[i];
+                if (v[i] > 0.0) Rlo[B.offR + (size_t)j * B.rs + i] = (T)r;
+                else Rhi[B.offR + (size_t)j * B.rs + i] = (T)r;
+            }
+            d[B.offd + j] = (T)hd[j];
+            invd[B.offd + j] = hd[j] > 0.0 ? (T)(1.0 / hd[j]) : T(0);
+        }
+        for (int j = 0; j < B.np; ++j)
+            for (int m = 0; m < M; ++m) {
+                Ut[B.offU + (size_t)j * M + m] = (T)hU[(size_t)j * M + m];
+                Um[B.offU + (size_t)m * B.np + j] = (T)hU[(size_t)j * M + m];
+            }
+    }
+    int rc;
+    if ((rc = upload(&out.V, V)) || (rc = upload(&out.Rlo, Rlo)) || (rc = upload(&out.Rhi, Rhi)) ||
+        (rc = upload(&out.d, d)) || (rc = upload(&out.invd, invd)) || (rc = upload(&out.Ut, Ut)) ||
+        (rc = upload(&out.Um, Um)))
+        return rc;
+    return ASM_OK;
+}
+
+bool all_finite(const double *x, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+namespace {
+
+// Read the recorded event pairs (synchronises the stream) into the totals.
+int drain_events(asm_problem *p)
+{
+    if (p->ev_used == 0) return ASM_OK;
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return ASM_ERR_CUDA;
+    for (size_t i = 0; i + 1 < p->ev_used; i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->ev_pool[i], p->ev_pool[i + 1]) != cudaSuccess) return ASM_ERR_CUDA;
+        p->timed_ms += ms;
+        ++p->timed_launches;
+    }
+    p->ev_used = 0;
+    return ASM_OK;
+}
+
+cudaEvent_t next_event(asm_problem *p)
+{
+    if (p->ev_used == p->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        p->ev_pool.push_back(e);
+    }
+    return p->ev_pool[p->ev_used++];
+}
+
+template <class T>
+SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout &L, int chains)
+{
+    SweepParams<T> sp{};
+    sp.M = p->M;
+    sp.N = p->N;
+    sp.S = p->team;
+    sp.n_levels = p->n_levels;
+    sp.level_first = p->d_level_first;
+    sp.level_nblocks = p->d_level_nblocks;
+    sp.blocks = p->d_blocks;
+    sp.pd.V = (const T *)b.V;
+    sp.pd.Rlo = (const T *)b.Rlo;
+    sp.pd.Rhi = (const T *)b.Rhi;
+    sp.pd.d = (const T *)b.d;
+    sp.pd.invd = (const T *)b.invd;
+    sp.pd.Ut = (const T *)b.Ut;
+    sp.pd.Um = (const T *)b.Um;
+    char *ws = (char *)p->ws;
+    sp.F = (T *)(ws + L.F);
+    sp.ldF = L.ldF;
+    sp.R = (T *)(ws + L.R);
+    sp.ldR = L.ldR;
+    sp.S1 = (double *)(ws + L.S1);
+    sp.S2 = (double *)(ws + L.S2);
+    sp.chains = chains;
+    sp.seed = p->seed;
+    sp.problem_id = 0;
+    sp.counters = (Counters *)(ws + L.counters);
+    sp.cpad = round_up_int(std::max(p->max_np, 1), 32);
+    sp.mpad = round_up_int(p->M, 32);
+    return sp;
+}
+
+int pick_kv(int max_nb, int vec, int S, int kmax)
+{
+    int need = (max_nb + vec * S - 1) / (vec * S);
+    int kv = 1;
+    while (kv < need) kv <<= 1;
+    return kv <= kmax ? kv : -1;
+}
+
+template <class T>
+int run_sweeps(asm_problem *p, const WsLayout &L, int chains, long long s_begin, long long s_end,
+               long long burn_abs)
+{
+    const PrecBuffers &b = sizeof(T) == 8 ? p->b64 : p->b32;
+    SweepParams<T> sp = make_params<T>(p, b, L, chains);
+    sp.burn_in = burn_abs;
+    const int vec = 16 / (int)sizeof(T);
+    const int kv = pick_kv(p->max_nb, vec, sp.S, sizeof(T) == 8 ? kMaxKvF64 : kMaxKvF32);
+    if (kv < 0) return ASM_ERR_TOO_LARGE;
+    char *ws = (char *)p->ws;
+    long long s = s_begin;
+    while (s < s_end) {
+        const long long seg = std::min<long long>(kRefreshPeriod - (s % kRefreshPeriod), s_end - s);
+        sp.sweep0 = s;
+        sp.nsweeps = seg;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (p->timing) {
+            if (p->ev_used + 2 > 4096 && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
+            e0 = next_event(p);
+            e1 = next_event(p);
+            if (!e0 || !e1 || cudaEventRecord(e0, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
+        }
+        cudaError_t e;
+        if constexpr (sizeof(T) == 8) e = launch_sweeps_f64(sp, kv, 4, p->stream);
+        else e = launch_sweeps_f32(sp, kv, 4, p->stream);
+        if (e != cudaSuccess) return ASM_ERR_CUDA;
+        if (p->timing && cudaEventRecord(e1, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
+        ++p->sweep_launches;
+        s += seg;
+        if (s % kRefreshPeriod == 0) {
+            refresh_kernel<T><<<chains, 128, sizeof(double) * p->N, p->stream>>>(
+                p->M, p->N, p->d_KtT, p->d_gt, sp.F, sp.ldF, sp.R, sp.ldR, (double *)(ws + L.chi2),
+                sp.counters, 1);
+            if (cudaGetLastError() != cudaSuccess) return ASM_ERR_CUDA;
+            ++p->other_launches;
+        }
+    }
+    return ASM_OK;
+}
+
+template <class T>
+int init_chains(asm_problem *p, const WsLayout &L, int chains)
+{
+    char *ws = (char *)p->ws;
+    if (cudaMemsetAsync(ws + L.counters, 0, sizeof(Counters), p->stream) != cudaSuccess) return ASM_ERR_CUDA;
+    const long long tot = (long long)chains * std::max(L.ldF, p->N);
+    init_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, p->stream>>>(
+        (T *)(ws + L.F), L.ldF, p->N, p->f0, (double *)(ws + L.S1), (double *)(ws + L.S2), chains);
+    if (cudaGetLastError() != cudaSuccess) return ASM_ERR_CUDA;
+    if (cudaMemsetAsync(ws + L.R, 0, (size_t)chains * L.ldR * sizeof(T), p->stream) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    refresh_kernel<T><<<chains, 128, sizeof(double) * p->N, p->stream>>>(
+        p->M, p->N, p->d_KtT, p->d_gt, (const T *)(ws + L.F), L.ldF, (T *)(ws + L.R), L.ldR,
+        (double *)(ws + L.chi2), (Counters *)(ws + L.counters), 0);
+    if (cudaGetLastError() != cudaSuccess) return ASM_ERR_CUDA;
+    p->other_launches += 2;
+    return ASM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *asm_error_string(int code)
+{
+    switch (code) {
+    case ASM_OK: return "ok";
+    case ASM_ERR_SHAPE: return "inconsistent sizes or block partition";
+    case ASM_ERR_NOT_SPD: return "covariance is not symmetric positive definite";
+    case ASM_ERR_NONFINITE: return "non-finite input";
+    case ASM_ERR_IMPROPER: return "improper zero mode: f >= 0 does not bound a flat direction";
+    case ASM_ERR_CUDA: return "CUDA, cuBLAS or cuSOLVER call failed";
+    case ASM_ERR_STATE: return "call out of order";
+    case ASM_ERR_ARG: return "invalid argument";
+    case ASM_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case ASM_ERR_TOO_LARGE: return "block larger than the compiled register tile";
+    default: return "unknown error";
+    }
+}
+
+int asm_setup(const asm_desc *ds, asm_problem **out)
+{
+    if (!ds || !out) return ASM_ERR_ARG;
+    *out = nullptr;
+    const int M = ds->M, N = ds->N;
+    if (M < 1 || N < 1 || ds->n_levels < 1 || !ds->level_nblocks || !ds->block_start) return ASM_ERR_SHAPE;
+    const bool given = ds->Kt && ds->gt && ds->d && ds->V && ds->U;
+    if (!given && (!ds->K || !ds->G || !ds->C)) return ASM_ERR_ARG;
+    asm_problem *p = new (std::nothrow) asm_problem;
+    if (!p) return ASM_ERR_ARG;
+    p->M = M;
+    p->N = N;
+    p->n_levels = ds->n_levels;
+    int nb = 0;
+    for (int l = 0; l < ds->n_levels; ++l) {
+        if (ds->level_nblocks[l] < 1) { delete p; return ASM_ERR_SHAPE; }
+        p->level_first.push_back(nb);
+        p->level_nblocks.push_back(ds->level_nblocks[l]);
+        nb += ds->level_nblocks[l];
+    }
+    p->n_blocks = nb;
+    long long oV = 0, oR = 0, od = 0, oU = 0;
+    for (int l = 0; l < ds->n_levels; ++l) {
+        const int *st = ds->block_start + p->level_first[l];
+        for (int b = 0; b < ds->level_nblocks[l]; ++b) {
+            const int s0 = st[b], s1 = b + 1 < ds->level_nblocks[l] ? st[b + 1] : N;
+            if ((b == 0 && s0 != 0) || s1 <= s0 || s1 > N) { delete p; return ASM_ERR_SHAPE; }
+            BlockDesc B{};
+            B.start = s0;
+            B.n = s1 - s0;
+            B.np = std::min(M, B.n);
+            B.rs = round_up_int(B.n, kRowAlign);
+            B.offV = oV; oV += (long long)B.n * B.rs;
+            B.offR = oR; oR += (long long)(B.n + 1) * B.rs;
+            B.offd = od; od += B.n;
+            B.offU = oU; oU += (long long)B.np * M;
+            p->blocks.push_back(B);
+            p->max_nb = std::max(p->max_nb, B.n);
+            p->max_np = std::max(p->max_np, B.np);
+        }
+    }
+    p->totV = oV; p->totR = oR; p->totd = od; p->totU = oU;
+    p->w.assign(N, 1.0);
+    if (ds->w) {
+        if (!all_finite(ds->w, N)) { delete p; return ASM_ERR_NONFINITE; }
+        for (int i = 0; i < N; ++i) p->w[i] = ds->w[i];
+    }
+
+    HostFactors hf;
+    int rc = ASM_OK;
+    if (given) {
+        if (!all_finite(ds->Kt, (size_t)M * N) || !all_finite(ds->gt, M)) { delete p; return ASM_ERR_NONFINITE; }
+        hf.Kt.assign(ds->Kt, ds->Kt + (size_t)M * N);
+        hf.gt.assign(ds->gt, ds->gt + M);
+        const double *dd = ds->d, *dv = ds->V, *du = ds->U;
+        hf.d.resize(nb); hf.V.resize(nb); hf.U.resize(nb);
+        for (int b = 0; b < nb; ++b) {
+            const BlockDesc &B = p->blocks[b];
+            hf.d[b].assign(dd, dd + B.n); dd += B.n;
+            hf.V[b].assign(dv, dv + (size_t)B.n * B.n); dv += (size_t)B.n * B.n;
+            hf.U[b].assign(du, du + (size_t)B.np * M); du += (size_t)B.np * M;
+        }
+    } else {
+        if (!all_finite(ds->K, (size_t)M * N) || !all_finite(ds->G, M) || !all_finite(ds->C, (size_t)M * M)) {
+            delete p;
+            return ASM_ERR_NONFINITE;
+        }
+        rc = device_factorize(ds, p, hf);
+        if (rc != ASM_OK) { delete p; return rc; }
+    }
+    // properness: every zero mode must change sign (both bounds finite)
+    for (int b = 0; b < nb; ++b) {
+        const BlockDesc &B = p->blocks[b];
+        for (int j = 0; j < B.n; ++j) {
+            if (hf.d[b][j] > 0.0) continue;
+            const double *v = &hf.V[b][(size_t)j * B.n];
+            double vmax = 0.0;
+            for (int i = 0; i < B.n; ++i) vmax = std::max(vmax, std::fabs(v[i]));
+            bool pos = false, neg = false;
+            for (int i = 0; i < B.n; ++i) {
+                if (std::fabs(v[i]) < 0x1p-40 * vmax) continue;
+                pos |= v[i] > 0.0;
+                neg |= v[i] < 0.0;
+            }
+            if (!(pos && neg)) { delete p; return ASM_ERR_IMPROPER; }
+        }
+    }
+    // starting scale: s* = argmin_{s >= 0} |g~ - s K~ 1|^2 (flat default model)
+    {
+        double num = 0.0, den = 0.0;
+        for (int i = 0; i < M; ++i) {
+            double k = 0.0;
+            for (int j = 0; j < N; ++j) k += hf.Kt[(size_t)i * N + j];
+            num += k * hf.gt[i];
+            den += k * k;
+        }
+        double s = den > 0.0 ? num / den : 0.0;
+        if (!(s > 0.0) || !std::isfinite(s)) s = 1.0 / N;
+        p->f0 = s;
+    }
+    std::vector<double> KtT((size_t)N * M);
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < N; ++j) KtT[(size_t)j * M + i] = hf.Kt[(size_t)i * N + j];
+    std::vector<int> lf(p->level_first), ln(p->level_nblocks);
+    if ((rc = upload((void **)&p->d_KtT, KtT)) || (rc = upload((void **)&p->d_gt, hf.gt)) ||
+        (rc = upload((void **)&p->d_level_first, lf)) || (rc = upload((void **)&p->d_level_nblocks, ln)) ||
+        (rc = upload((void **)&p->d_blocks, p->blocks)) || (rc = build_precision<double>(p, hf, p->b64)) ||
+        (rc = build_precision<float>(p, hf, p->b32))) {
+        asm_destroy(p);
+        return rc;
+    }
+    const char *team = std::getenv("ASM_TEAM_LANES");
+    if (team) {
+        const int t = std::atoi(team);
+        if (t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32) p->team = t;
+    }
+    *out = p;
+    return ASM_OK;
+}
+
+size_t asm_workspace_bytes(const asm_problem *p, int chains, int precision)
+{
+    if (!p || chains < 1 || (precision != ASM_FP64 && precision != ASM_MIXED)) return 0;
+    return ws_layout(p, chains, precision).total;
+}
+
+int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t seed, int precision,
+               uint32_t flags, void *d_workspace, size_t workspace_bytes, void *stream)
+{
+    if (!p || chains < 1 || burn_in < 0 || sweeps < 0) return ASM_ERR_ARG;
+    if (precision != ASM_FP64 && precision != ASM_MIXED) return ASM_ERR_ARG;
+    const WsLayout L = ws_layout(p, chains, precision);
+    if (!d_workspace || workspace_bytes < L.total || ((uintptr_t)d_workspace & 255)) return ASM_ERR_WORKSPACE;
+    const bool cont = (flags & ASM_SAMPLE_CONTINUE) != 0;
+    if (cont && (!p->have_run || p->chains != chains || p->precision != precision || p->ws != d_workspace ||
+                 p->seed != seed))
+        return ASM_ERR_STATE;
+    if (p->ev_used && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
+    p->stream = (cudaStream_t)stream;
+    p->timing = (flags & ASM_SAMPLE_TIMING) != 0;
+    p->ws = d_workspace;
+    p->ws_bytes = workspace_bytes;
+    int rc;
+    if (!cont) {
+        p->chains = chains;
+        p->precision = precision;
+        p->seed = seed;
+        p->sweeps_done = 0;
+        p->kept = 0;
+        p->sweep_launches = p->other_launches = p->timed_launches = 0;
+        p->timed_ms = 0.0;
+        rc = precision == ASM_FP64 ? init_chains<double>(p, L, chains) : init_chains<float>(p, L, chains);
+        if (rc != ASM_OK) return rc;
+        p->have_run = true;
+    }
+    const long long s0 = p->sweeps_done, s1 = s0 + burn_in + sweeps, burn_abs = s0 + burn_in;
+    rc = precision == ASM_FP64 ? run_sweeps<double>(p, L, chains, s0, s1, burn_abs)
+                               : run_sweeps<float>(p, L, chains, s0, s1, burn_abs);
+    if (rc != ASM_OK) return rc;
+    p->sweeps_done = s1;
+    p->kept += sweeps;
+    return ASM_OK;
+}
+
+int asm_average(asm_problem *p, double *mean_A, double *sem_A, double *ess, double *mean_fbar)
+{
+    if (!p) return ASM_ERR_ARG;
+    if (!p->have_run || p->kept < 1) return ASM_ERR_STATE;
+    const WsLayout L = ws_layout(p, p->chains, p->precision);
+    const int N = p->N;
+    double *d = nullptr;
+    if (cudaMalloc(&d, sizeof(double) * 3 * N) != cudaSuccess) return ASM_ERR_CUDA;
+    char *ws = (char *)p->ws;
+    ++p->other_launches;
+    reduce_kernel<<<(N + 127) / 128, 128, 0, p->stream>>>((const double *)(ws + L.S1), (const double *)(ws + L.S2),
+                                                          p->chains, N, (double)p->kept, d, d + N, d + 2 * N);
+    std::vector<double> h((size_t)3 * N);
+    int rc = ASM_OK;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h.data(), d, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+        rc = ASM_ERR_CUDA;
+    cudaFree(d);
+    if (rc != ASM_OK) return rc;
+    for (int n = 0; n < N; ++n) {
+        const double mu = h[n], s2 = h[N + n], m2 = h[2 * N + n];
+        const double var = std::max(m2 - mu * mu, 0.0);
+        if (mean_fbar) mean_fbar[n] = mu;
+        if (mean_A) mean_A[n] = mu / p->w[n];
+        if (sem_A) sem_A[n] = std::sqrt(s2) / p->w[n];
+        if (ess) ess[n] = s2 > 0.0 ? var / s2 : NAN;
+    }
+    return ASM_OK;
+}
+
+int asm_chain_state(asm_problem *p, double *f, double *chi2)
+{
+    if (!p) return ASM_ERR_ARG;
+    if (!p->have_run) return ASM_ERR_STATE;
+    const WsLayout L = ws_layout(p, p->chains, p->precision);
+    const size_t es = p->precision == ASM_FP64 ? 8 : 4;
+    const char *ws = (const char *)p->ws;
+    std::vector<unsigned char> hF((size_t)p->chains * L.ldF * es), hR((size_t)p->chains * L.ldR * es);
+    if (cudaMemcpyAsync(hF.data(), ws + L.F, hF.size(), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(hR.data(), ws + L.R, hR.size(), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    for (int q = 0; q < p->chains; ++q) {
+        if (f)
+            for (int n = 0; n < p->N; ++n) {
+                const size_t i = (size_t)q * L.ldF + n;
+                f[(size_t)q * p->N + n] = es == 8 ? ((const double *)hF.data())[i] : ((const float *)hF.data())[i];
+            }
+        if (chi2) {
+            double s = 0.0;
+            for (int m = 0; m < p->M; ++m) {
+                const size_t i = (size_t)q * L.ldR + m;
+                const double r = es == 8 ? ((const double *)hR.data())[i] : ((const float *)hR.data())[i];
+                s += r * r;
+            }
+            chi2[q] = s;
+        }
+    }
+    return ASM_OK;
+}
+
+int asm_status(asm_problem *p, asm_stats *out)
+{
+    if (!p || !out) return ASM_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    if (!p->have_run) return ASM_ERR_STATE;
+    if (drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
+    Counters c{};
+    if (cudaMemcpyAsync(&c, p->ws, sizeof(c), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    out->chains = p->chains;
+    out->sweeps_done = p->sweeps_done;
+    out->kept_sweeps = p->kept;
+    out->precision = p->precision;
+    out->degenerate_moves = (int64_t)c.degenerate;
+    out->zero_mode_moves = (int64_t)c.zero_mode;
+    out->tail_capped = (int64_t)c.tail_capped;
+    out->nonfinite_moves = (int64_t)c.nonfinite;
+    double drift;
+    std::memcpy(&drift, &c.drift_bits, sizeof(drift));
+    out->max_resync_drift = drift;
+    out->sweep_launches = p->sweep_launches;
+    out->other_launches = p->other_launches;
+    out->timed_launches = p->timed_launches;
+    out->sweep_kernel_ms = p->timed_ms;
+    return ASM_OK;
+}
+
+void asm_destroy(asm_problem *p)
+{
+    if (!p) return;
+    void *ptrs[] = {p->d_level_first, p->d_level_nblocks, p->d_blocks, p->d_KtT, p->d_gt};
+    for (void *x : ptrs)
+        if (x) cudaFree(x);
+    free_prec(p->b64);
+    free_prec(p->b32);
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,397 @@
+// asm_sweep.cuh -- the chain kernel of blocked modes sampling (Ghanem & Koch,
+// arXiv:1912.01379, Sec. IV.B-C) for sm_103a.
+//
+// Layout.  A team of S lanes (S a power of two, S <= 32) runs one chain; a warp
+// runs 32/S chains.  While a block is visited, the team keeps the block's part
+// of the chain state f in registers: lane s holds the 16-byte vectors
+// k*S + s (k < KV) of the block.  Mode rows (V, and the masked reciprocals
+// Rlo/Rhi that give the bounds of Eq. modeLimits) are read as 16-byte vectors
+// through the read-only cache; every chain of the same problem reads the same
+// rows at the same time.  The tracked residual r~ = g~ - K~ f and the block's
+// projections c_j = U_j^T r~ live in shared memory.
+//
+// One move of mode j (Sec. IV.B, "sample e_i' from a univariate Gaussian ...
+// truncated to the interval for which f' >= 0"):
+//   [lo, hi]  = interval of delta from the previous pass (team max/min reduce)
+//   delta     ~ N(c_j/d_j, 1/d_j^2) on [lo, hi] by the inverse CDF (flat if d_j = 0)
+//   pass      f += delta V_j, clamp at 0, and the bounds of mode j+1 in the same
+//             sweep over the registers
+//   w_j       = d_j delta  (the residual moves by -w_j U_j; c_j is not needed again)
+// Block entry computes c = U_b^T r~, block exit applies r~ -= U_b w.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "asm_internal.h"
+
+namespace asmgb {
+
+// --------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11): counter-based, so every move's uniform
+// is a pure function of (seed, move, sweep, chain, problem).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64_10(unsigned long long &c0, unsigned long long &c1,
+                                              unsigned long long &c2, unsigned long long &c3,
+                                              unsigned long long k0, unsigned long long k1)
+{
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += W0; k1 += W1; }
+        const unsigned long long hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        const unsigned long long hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const unsigned long long y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
+        c0 = y0; c1 = lo1; c2 = y2; c3 = lo0;
+    }
+}
+
+// u in (0,1) on the grid (k + 1/2) 2^-52 (FP64) or (k + 1/2) 2^-23 (FP32, the
+// top 23 bits of the same word); 1 - u is exact in both.
+template <class T> __device__ __forceinline__ T uniform_from(unsigned long long w);
+template <> __device__ __forceinline__ double uniform_from<double>(unsigned long long w)
+{
+    return ((double)(w >> 12) + 0.5) * 0x1p-52;
+}
+template <> __device__ __forceinline__ float uniform_from<float>(unsigned long long w)
+{
+    return ((float)(unsigned)(w >> 41) + 0.5f) * 0x1p-23f;
+}
+
+// --------------------------------------------------------------------------
+// precision-overloaded math (CUDA math library calls)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double m_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float m_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double m_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float m_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double m_min(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float m_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double m_phi(double x) { return normcdf(x); }
+__device__ __forceinline__ float m_phi(float x) { return normcdff(x); }
+__device__ __forceinline__ double m_phiinv(double p) { return normcdfinv(p); }
+__device__ __forceinline__ float m_phiinv(float p) { return normcdfinvf(p); }
+__device__ __forceinline__ double m_erfcx(double x) { return erfcx(x); }
+__device__ __forceinline__ float m_erfcx(float x) { return erfcxf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double m_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float m_abs(float x) { return fabsf(x); }
+
+template <class T> struct TailTraits;
+template <> struct TailTraits<double> {
+    static constexpr double tol = 1e-14;
+    static constexpr int nmax = 40;
+};
+template <> struct TailTraits<float> {
+    static constexpr float tol = 2e-6f;
+    static constexpr int nmax = 16;
+};
+
+// x ~ N(0,1) restricted to [a, b], 0 <= a < b <= inf, by Q(x) = (1-u)Q(a) + uQ(b).
+// Returns the offset y = x - a.  For a >= 5 the equation is solved for y by
+// Newton's method on log Q (concave, so the iterates are monotone after the
+// first step), with Q(b)/Q(a) formed through erfcx to keep narrow intervals
+// accurate.
+template <class T>
+__device__ __forceinline__ T right_tail(T a, T b, T u, int &capped)
+{
+    const T kRsqrt2 = T(0.70710678118654752440);
+    const T kSqrtPiOver2 = T(1.25331413731550025121);
+    T y;
+    if (a < T(5)) {
+        const T qa = m_phi(-a);
+        const T qb = isinf(b) ? T(0) : m_phi(-b);
+        const T q = (T(1) - u) * qa + u * qb;
+        y = -m_phiinv(q) - a;
+    } else {
+        const T exa = m_erfcx(a * kRsqrt2);
+        T r = T(0), em = T(-1);
+        if (!isinf(b)) {
+            const T lr = m_log(m_erfcx(b * kRsqrt2) / exa) - T(0.5) * (b - a) * (b + a);
+            r = m_exp(lr);
+            em = m_expm1(lr);
+        }
+        const T dt = r < T(0.5) ? m_log((T(1) - u) + u * r) : m_log1p(u * em);
+        y = -dt / a;
+        int it = 0;
+        for (; it < TailTraits<T>::nmax; ++it) {
+            const T exy = m_erfcx((a + y) * kRsqrt2);
+            const T g = m_log(exy / exa) - y * (a + T(0.5) * y) - dt;
+            const T step = -g * exy * kSqrtPiOver2;   // g / g', g' = -sqrt(2/pi)/erfcx
+            y -= step;
+            if (m_abs(step) <= TailTraits<T>::tol * (y + T(1) / a)) break;
+        }
+        if (it == TailTraits<T>::nmax) ++capped;
+    }
+    y = m_max(y, T(0));
+    y = m_min(y, b - a);
+    return y;
+}
+
+// delta ~ N(c/d, 1/d^2) restricted to [lo, hi] (lo < hi), by the inverse CDF at u.
+// In standard units x = d delta - c the interval is [a, b] = [d lo - c, d hi - c].
+template <class T>
+__device__ __forceinline__ T tn_step(T c, T d, T invd, T lo, T hi, T u, int &capped)
+{
+    const T a = m_fma(lo, d, -c);
+    const T b = m_fma(hi, d, -c);
+    T delta;
+    if (a >= T(0)) {
+        delta = lo + invd * right_tail(a, b, u, capped);
+    } else if (b <= T(0)) {
+        delta = hi - invd * right_tail(-b, -a, T(1) - u, capped);
+    } else {
+        const T p = (T(1) - u) * m_phi(a) + u * m_phi(b);
+        T x;
+        if (p <= T(0.5)) {
+            x = m_phiinv(p);
+        } else {
+            x = -m_phiinv((T(1) - u) * m_phi(-a) + u * m_phi(-b));
+        }
+        delta = (x + c) * invd;
+    }
+    return m_min(m_max(delta, lo), hi);
+}
+
+// --------------------------------------------------------------------------
+// 16-byte vector loads through the read-only path
+// --------------------------------------------------------------------------
+template <class T> struct VecOf;
+template <> struct VecOf<float> { static constexpr int n = 4; };
+template <> struct VecOf<double> { static constexpr int n = 2; };
+
+__device__ __forceinline__ void ldv(const float *p, float (&o)[4])
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ldv(const double *p, double (&o)[2])
+{
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    o[0] = v.x; o[1] = v.y;
+}
+
+// f += delta * V (clamped at 0), then the bounds of the next mode from the
+// updated f: lo = max over V>0 of -f/V, hi = min over V<0 of -f/V.  Rlo/Rhi
+// hold -1/V where V has the right sign and NaN elsewhere; fmax/fmin drop NaN.
+template <class T, int KV>
+__device__ __forceinline__ void fused_pass(T (&f)[KV][VecOf<T>::n], T delta,
+                                           const T *__restrict__ vrow, const T *__restrict__ rlrow,
+                                           const T *__restrict__ rhrow, int kcnt, int sl, int S,
+                                           T &lo, T &hi)
+{
+    constexpr int VEC = VecOf<T>::n;
+    T la[VEC], ha[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+        la[v] = -CUDART_INF_F;
+        ha[v] = CUDART_INF_F;
+    }
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+        if (k < kcnt) {
+            const int idx = VEC * (k * S + sl);
+            T vv[VEC], rl[VEC], rh[VEC];
+            ldv(vrow + idx, vv);
+            ldv(rlrow + idx, rl);
+            ldv(rhrow + idx, rh);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                T x = m_fma(delta, vv[v], f[k][v]);
+                x = m_max(x, T(0));
+                f[k][v] = x;
+                la[v] = m_max(la[v], x * rl[v]);
+                ha[v] = m_min(ha[v], x * rh[v]);
+            }
+        }
+    }
+    lo = la[0];
+    hi = ha[0];
+#pragma unroll
+    for (int v = 1; v < VEC; ++v) {
+        lo = m_max(lo, la[v]);
+        hi = m_min(hi, ha[v]);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T shfl_xor(T v, int off)
+{
+    return __shfl_xor_sync(0xffffffffu, v, off);
+}
+
+// --------------------------------------------------------------------------
+// the sweep kernel: sweeps [sweep0, sweep0 + nsweeps) of every chain
+// --------------------------------------------------------------------------
+template <class T, int KV>
+__global__ void __launch_bounds__(128) sweep_kernel(const SweepParams<T> p)
+{
+    constexpr int VEC = VecOf<T>::n;
+    const int lane = threadIdx.x & 31;
+    const int wcta = threadIdx.x >> 5;
+    const int S = p.S;
+    const int TW = 32 / S;
+    const int team = lane / S;
+    const int sl = lane - team * S;
+    const int team_base = team * S;
+    const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + wcta;
+    const long long q_raw = gwarp * TW + team;
+    const bool active = q_raw < p.chains;
+    const long long q = active ? q_raw : (long long)p.chains - 1;  // idle teams shadow a real chain, write nothing
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *csm = reinterpret_cast<T *>(smem_raw) + (size_t)(wcta * TW + team) * (2 * p.cpad + p.mpad);
+    T *wsm = csm + p.cpad;
+    T *rsm = wsm + p.cpad;
+
+    T *Rq = p.R + (size_t)q * p.ldR;
+    for (int m = sl; m < p.M; m += S) rsm[m] = Rq[m];
+    T *Fq = p.F + (size_t)q * p.ldF;
+    double *S1q = p.S1 + (size_t)q * p.N;
+    double *S2q = p.S2 + (size_t)q * p.N;
+    __syncwarp();
+
+    T f[KV][VEC];
+    unsigned long long n_deg = 0, n_zero = 0, n_bad = 0;
+    int capped = 0;
+    unsigned long long rw0 = 0, rw1 = 0, rw2 = 0, rw3 = 0;
+
+    for (long long s = p.sweep0; s < p.sweep0 + p.nsweeps; ++s) {
+        // level of this sweep: same for every chain of the problem (Sec. IV.C)
+        unsigned long long l0 = ~0ull, l1 = (unsigned long long)s, l2 = 0ull, l3 = p.problem_id;
+        philox4x64_10(l0, l1, l2, l3, p.seed, 0ull);
+        int level = (int)(uniform_from<double>(l0) * p.n_levels);
+        if (level >= p.n_levels) level = p.n_levels - 1;
+        const bool keep = s >= p.burn_in;
+        long long win = -1;  // first move index covered by this lane's Philox words
+        const int nb = p.level_nblocks[level];
+        const BlockDesc *bd = p.blocks + p.level_first[level];
+
+        for (int bi = 0; bi < nb; ++bi) {
+            const BlockDesc B = bd[bi];
+            const int kcnt = (B.n + VEC * S - 1) / (VEC * S);
+            // entry: the block's f into registers
+#pragma unroll
+            for (int k = 0; k < KV; ++k)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    const int nl = VEC * (k * S + sl) + v;
+                    f[k][v] = (k < kcnt && nl < B.n) ? Fq[B.start + nl] : T(0);
+                }
+            // c = U_b^T r~ (lanes split the modes)
+            const T *Um = p.pd.Um + B.offU;
+            for (int j = sl; j < B.np; j += S) {
+                T a = T(0);
+                for (int m = 0; m < p.M; ++m) a = m_fma(__ldg(Um + (size_t)m * B.np + j), rsm[m], a);
+                csm[j] = a;
+            }
+            __syncwarp();
+
+            const T *Vb = p.pd.V + B.offV;
+            const T *Rl = p.pd.Rlo + B.offR;
+            const T *Rh = p.pd.Rhi + B.offR;
+            const T *db = p.pd.d + B.offd;
+            const T *idb = p.pd.invd + B.offd;
+            T lo, hi;
+            fused_pass<T, KV>(f, T(0), Vb, Rl, Rh, kcnt, sl, S, lo, hi);  // bounds of mode 0
+            for (int j = 0; j < B.n; ++j) {
+                for (int off = 1; off < S; off <<= 1) {
+                    lo = m_max(lo, shfl_xor(lo, off));
+                    hi = m_min(hi, shfl_xor(hi, off));
+                }
+                // uniform of move t: word t%4 of Philox(ctr = {t/4, s, q, problem})
+                const int t = B.start + j;
+                if (win < 0 || t >= win + 4 * S) {
+                    win = (long long)(t / (4 * S)) * (4 * S);
+                    unsigned long long c0 = (unsigned long long)(win >> 2) + (unsigned long long)sl;
+                    unsigned long long c1 = (unsigned long long)s, c2 = (unsigned long long)q,
+                                       c3 = p.problem_id;
+                    philox4x64_10(c0, c1, c2, c3, p.seed, 0ull);
+                    rw0 = c0; rw1 = c1; rw2 = c2; rw3 = c3;
+                }
+                const int sel = t & 3;
+                const unsigned long long mine = sel == 0 ? rw0 : sel == 1 ? rw1 : sel == 2 ? rw2 : rw3;
+                const int src = (t >> 2) - (int)(win >> 2);
+                const unsigned long long word = __shfl_sync(0xffffffffu, mine, team_base + src);
+                const T u = uniform_from<T>(word);
+
+                const T dj = __ldg(db + j);
+                T delta;
+                if (!(hi > lo)) {
+                    delta = T(0);
+                    ++n_deg;
+                } else if (dj == T(0)) {
+                    delta = m_fma(u, hi - lo, lo);
+                    ++n_zero;
+                } else {
+                    delta = tn_step<T>(csm[j], dj, __ldg(idb + j), lo, hi, u, capped);
+                }
+                if (!isfinite(delta)) {
+                    delta = T(0);
+                    ++n_bad;
+                }
+                if (j < B.np && sl == 0) wsm[j] = dj * delta;
+                fused_pass<T, KV>(f, delta, Vb + (size_t)j * B.rs, Rl + (size_t)(j + 1) * B.rs,
+                                  Rh + (size_t)(j + 1) * B.rs, kcnt, sl, S, lo, hi);
+            }
+            __syncwarp();
+            // exit: r~ -= U_b w (lanes split the data points)
+            const T *Ut = p.pd.Ut + B.offU;
+            for (int m = sl; m < p.M; m += S) {
+                T a = T(0);
+                for (int j = 0; j < B.np; ++j) a = m_fma(__ldg(Ut + (size_t)j * p.M + m), wsm[j], a);
+                rsm[m] -= a;
+            }
+            // write the block back and accumulate the kept sweep
+#pragma unroll
+            for (int k = 0; k < KV; ++k)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    const int nl = VEC * (k * S + sl) + v;
+                    if (active && k < kcnt && nl < B.n) {
+                        const int n = B.start + nl;
+                        Fq[n] = f[k][v];
+                        if (keep) {
+                            const double x = (double)f[k][v];
+                            S1q[n] += x;
+                            S2q[n] += x * x;
+                        }
+                    }
+                }
+            __syncwarp();
+        }
+    }
+    if (active) {
+        for (int m = sl; m < p.M; m += S) Rq[m] = rsm[m];
+        if (sl == 0) {
+            if (n_deg) atomicAdd(&p.counters->degenerate, n_deg);
+            if (n_zero) atomicAdd(&p.counters->zero_mode, n_zero);
+            if (n_bad) atomicAdd(&p.counters->nonfinite, n_bad);
+            if (capped) atomicAdd(&p.counters->tail_capped, (unsigned long long)capped);
+        }
+    }
+}
+
+template <class T, int KV>
+cudaError_t launch_sweep_kernel(const SweepParams<T> &p, int warps_per_cta, cudaStream_t stream)
+{
+    const int TW = 32 / p.S;
+    const long long warps = (p.chains + TW - 1) / TW;
+    const long long ctas = (warps + warps_per_cta - 1) / warps_per_cta;
+    const size_t smem = (size_t)warps_per_cta * TW * (2 * p.cpad + p.mpad) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    sweep_kernel<T, KV><<<(unsigned)ctas, 32 * warps_per_cta, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace asmgb

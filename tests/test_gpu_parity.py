@@ -1,0 +1,169 @@
+"""GPU parity of the CUDA sampler (through the C ABI) against the FP64 CPU oracle.
+
+* FP64 path, same singular vectors (the oracle's factors given to the library)
+  and the same Philox stream: chain states after every sweep agree with the
+  oracle's within 1e-9 relative (element by element).
+* Invariants: fbar >= 0 after every sweep; the residual the kernel tracks
+  incrementally equals |g~ - K~ f|^2 recomputed in FP64 within 1e-10 relative.
+* Long runs with the library's own factorisation (cuSOLVER): <fbar> agrees with
+  the oracle's within 4 combined Monte Carlo standard errors, in FP64 and in
+  the mixed FP32/FP64 path.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1912_01379_gb300 import asm
+from paper_1912_01379_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STEP_RTOL = 1e-9     # FP64 step-by-step tolerance (relative to the chain's max |f|)
+CHI2_RTOL = 1e-10    # tracked vs recomputed chi^2
+Z_MAX = 4.0          # long-run agreement in combined standard errors
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+    torch.cuda.synchronize()
+
+
+def _gpu_problem(p, factors=None, team=None):
+    old = os.environ.get("ASM_TEAM_LANES")
+    if team is not None:
+        os.environ["ASM_TEAM_LANES"] = str(team)
+    try:
+        return asm.Problem(p.K, p.G, p.C, p.levels, w=p.w, factors=factors)
+    finally:
+        if team is not None:
+            if old is None:
+                os.environ.pop("ASM_TEAM_LANES", None)
+            else:
+                os.environ["ASM_TEAM_LANES"] = old
+
+
+def _step_cases():
+    yield "plain_modes", W.plain_modes_problem()
+    # several levels, ragged blocks spanning more than one register tile,
+    # N > M (zero modes), a components level
+    yield "ragged_levels", W.small_problem(30, 150, seed=21, levels=[[0], [0, 37, 87], np.arange(150)[::10],
+                                                                    np.arange(150)])
+    yield "tall_M_gt_N", W.small_problem(40, 12, seed=22, levels=[[0], [0, 5]])
+    yield "bosonic", W.small_problem(25, 70, seed=23, levels=[[0], [0, 20, 45]], bosonic=True)
+
+
+@pytest.mark.parametrize("team", [32, 8])
+@pytest.mark.parametrize("case", list(range(4)))
+def test_fp64_matches_oracle_step_by_step(case, team):
+    name, p = list(_step_cases())[case]
+    op = O.OracleProblem(p.K, p.G, p.C, p.levels)
+    dec = op.decomposition()
+    chains, sweeps, seed = 7, 6, 1234 + case
+    ref = op.run(chains, 0, sweeps, seed=seed, trace_chains=chains)
+    gp = _gpu_problem(p, factors=dec, team=team)
+    for s in range(sweeps):
+        gp.sample(chains, 0, 1, seed, precision=asm.ASM_FP64, cont=s > 0)
+        f, chi2 = gp.chain_state()
+        want = ref["trace"][:, s, :]
+        scale = np.abs(want).max(axis=1, keepdims=True)
+        err = np.abs(f - want) / scale
+        assert err.max() <= STEP_RTOL, (name, team, s, err.max())
+        assert f.min() >= 0.0
+        exact = np.sum((dec.gt[None, :] - f @ dec.Kt.T) ** 2, axis=1)
+        assert np.allclose(chi2, exact, rtol=CHI2_RTOL, atol=0), (name, s)
+    st = gp.status()
+    assert st["nonfinite_moves"] == 0
+
+
+def test_fp64_full_size_sampled_chains():
+    """The blocked-modes workload at full size (N=400, M=100, 1024 chains) in the
+    launch configuration of the benchmark: sampled chains match the oracle."""
+    p = W.blocked_modes_problem()
+    op = O.OracleProblem(p.K, p.G, p.C, p.levels)
+    dec = op.decomposition()
+    chains, sweeps, seed = 1024, 3, 77
+    ref = op.run(chains, 0, sweeps, seed=seed, threads=0)
+    gp = _gpu_problem(p, factors=dec)
+    gp.sample(chains, 0, sweeps, seed, precision=asm.ASM_FP64)
+    f, chi2 = gp.chain_state()
+    idx = [0, 1, 333, 511, 512, 777, 1022, 1023]
+    want = ref["f_final"][idx]
+    err = np.abs(f[idx] - want) / np.abs(want).max(axis=1, keepdims=True)
+    assert err.max() <= STEP_RTOL, err.max()
+    assert np.allclose(chi2[idx], ref["chi2"][idx], rtol=1e-9)
+    assert f.min() >= 0.0
+
+
+def test_mixed_precision_tracks_fp64_over_one_sweep():
+    p = W.plain_modes_problem()
+    op = O.OracleProblem(p.K, p.G, p.C, p.levels)
+    dec = op.decomposition()
+    ref = op.run(16, 0, 1, seed=5)
+    gp = _gpu_problem(p, factors=dec)
+    gp.sample(16, 0, 1, 5, precision=asm.ASM_MIXED)
+    f, _ = gp.chain_state()
+    err = np.abs(f - ref["f_final"]) / np.abs(ref["f_final"]).max(axis=1, keepdims=True)
+    assert f.min() >= 0.0
+    assert np.median(err) < 1e-3, np.median(err)
+
+
+def _long_run(p, chains_gpu, chains_cpu, burn, sweeps, precision, seed):
+    op = O.OracleProblem(p.K, p.G, p.C, p.levels)
+    r = op.run(chains_cpu, burn, sweeps, seed=seed + 1, threads=0)
+    so = O.summarize(r["S1"], r["S2"], r["kept"], p.w)
+    gp = _gpu_problem(p)                   # library's own cuSOLVER factors
+    gp.sample(chains_gpu, burn, sweeps, seed, precision=precision)
+    sg = gp.average()
+    z = (sg["mean_fbar"] - so["mean_fbar"]) / np.hypot(sg["sem_fbar"], so["sem_fbar"])
+    return z, sg, so, gp.status()
+
+
+@pytest.mark.parametrize("precision", [asm.ASM_FP64, asm.ASM_MIXED])
+def test_long_run_plain_modes(precision):
+    p = W.plain_modes_problem()
+    z, sg, so, st = _long_run(p, 256, 64, 1000, 10000, precision, seed=11)
+    assert np.all(np.abs(z) < Z_MAX), np.abs(z).max()
+    assert st["nonfinite_moves"] == 0
+    assert np.allclose(sg["mean_A"], sg["mean_fbar"] / p.w)
+
+
+@pytest.mark.parametrize("precision", [asm.ASM_FP64, asm.ASM_MIXED])
+def test_long_run_blocked_modes(precision):
+    p = W.blocked_modes_problem()
+    z, sg, so, st = _long_run(p, 1024, 128, 300, 1500, precision, seed=12)
+    assert np.all(np.abs(z) < Z_MAX), np.abs(z).max()
+    assert st["nonfinite_moves"] == 0
+    assert st["max_resync_drift"] < (1e-8 if precision == asm.ASM_FP64 else 1e-2)
+
+
+def test_edge_cases_and_errors():
+    p = W.small_problem(10, 9, seed=3, levels=[[0], [0, 1, 8]])
+    gp = _gpu_problem(p)
+    gp.sample(1, 0, 3, 1, precision=asm.ASM_FP64)           # a single chain
+    f, _ = gp.chain_state()
+    assert f.shape == (1, 9) and f.min() >= 0
+    gp.sample(33, 2, 3, 1, precision=asm.ASM_MIXED)          # ragged last warp
+    r = gp.average()
+    assert np.all(np.isfinite(r["mean_A"]))
+    with pytest.raises(asm.ASMError):                        # continue with other chains
+        gp.sample(34, 0, 1, 1, precision=asm.ASM_MIXED, cont=True)
+    with pytest.raises(asm.ASMError, match="symmetric positive"):
+        asm.Problem(p.K, p.G, -p.C, p.levels)
+    with pytest.raises(asm.ASMError, match="partition"):
+        asm.Problem(p.K, p.G, p.C, [[2, 5]])
+    K = np.ones((2, 2)); K[:, 1] = -1.0
+    with pytest.raises(asm.ASMError, match="improper"):
+        asm.Problem(K, np.ones(2), np.eye(2), [[0]])
+    G = p.G.copy(); G[1] = np.inf
+    with pytest.raises(asm.ASMError, match="non-finite"):
+        asm.Problem(p.K, G, p.C, p.levels)
+    import torch
+    small = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(asm.ASMError, match="workspace"):
+        gp.sample(4, 0, 1, 1, workspace=small)
