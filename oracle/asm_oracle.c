@@ -10,7 +10,10 @@
  * Readings of the paper that this file fixes (all also listed in the design doc):
  *  R1 moves draw delta = e' - e from the 1-D conditional with ONE uniform u
  *     through the inverse CDF of the truncated normal (Sec. IV.A cites a
- *     rejection sampler; an inverse CDF samples the same distribution).
+ *     rejection sampler; an inverse CDF samples the same distribution).  The
+ *     inverse CDF is evaluated in the form that keeps delta - lo accurate
+ *     relative to hi - lo: Gauss-Legendre + Newton on intervals narrower than
+ *     the Gaussian's curvature, Phi^{-1} in the centre, log Q in the tails.
  *  R2 zero modes (d = 0, Sec. IV.B) are flat on their interval; singular
  *     values d <= d_1 max(M, n) 2^-52 count as zero.
  *  R3 the bounds of Eq. modeLimits are used as delta in [max_{V>0} -f/V,
@@ -159,13 +162,77 @@ static double ora_right_tail(double a, double b, double u, int *capped)
     return y;
 }
 
+/* Gauss-Legendre nodes and weights on [-1, 1] (8 points), from Newton's method
+ * on the Legendre polynomial P_8 evaluated by its three-term recurrence. */
+static double ora_gl_x[8], ora_gl_w[8];
+static int ora_gl_ready = 0;
+
+static void ora_gl_init(void)
+{
+    if (ora_gl_ready) return;
+    const int n = 8;
+    for (int i = 0; i < n; ++i) {
+        double x = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-17) break;
+        }
+        ora_gl_x[i] = x;
+        ora_gl_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    ora_gl_ready = 1;
+}
+
+/* I(t) = int_0^t exp(-a s - s^2/2) ds, the unnormalised CDF of N(0,1) on
+ * [a, a + w] measured from a, by 8-point Gauss-Legendre (relative error ~1e-16
+ * while t (|a| + t) <= 1/2). */
+static double ora_narrow_cdf(double a, double t)
+{
+    double acc = 0.0;
+    for (int i = 0; i < 8; ++i) {
+        double s = 0.5 * t * (1.0 + ora_gl_x[i]);
+        acc += ora_gl_w[i] * exp(-a * s - 0.5 * s * s);
+    }
+    return 0.5 * t * acc;
+}
+
+/* Narrow interval [a, a + w] (w (|a| + w) <= 1/2): the inverse CDF
+ * I(t) = u I(w) solved by Newton's method from the uniform guess t = u w.
+ * Returns the offset t from a with relative accuracy, however small w is. */
+static double ora_narrow(double a, double w, double u, int *capped)
+{
+    double target = u * ora_narrow_cdf(a, w), t = u * w;
+    int it;
+    for (it = 0; it < 60; ++it) {
+        double step = (ora_narrow_cdf(a, t) - target) / exp(-a * t - 0.5 * t * t);
+        t -= step;
+        if (t < 0.0) t = 0.0;
+        if (t > w) t = w;
+        if (fabs(step) <= 4e-16 * t || t == 0.0) break;
+    }
+    if (it == 60 && capped) ++*capped;
+    return t;
+}
+
 static double ora_truncnorm_impl(double mu, double sigma, double lo, double hi, double u,
                                  int *capped)
 {
     if (!(hi > lo)) return lo;
     double alpha = (lo - mu) / sigma, beta = (hi - mu) / sigma;
+    double wid = (hi - lo) / sigma;     /* interval width in units of sigma */
     double d;
-    if (alpha >= 0.0) {
+    if (isfinite(wid) && wid * (fabs(alpha) + wid) <= 0.5) {
+        /* nearly flat over the interval: Gauss-Legendre inverse CDF */
+        d = lo + sigma * ora_narrow(alpha, wid, u, capped);
+    } else if (alpha >= 0.0) {
         d = lo + sigma * ora_right_tail(alpha, beta, u, capped);
     } else if (beta <= 0.0) {
         d = hi - sigma * ora_right_tail(-beta, -alpha, 1.0 - u, capped);
@@ -188,6 +255,7 @@ static double ora_truncnorm_impl(double mu, double sigma, double lo, double hi, 
 
 double ora_truncnorm(double mu, double sigma, double lo, double hi, double u)
 {
+    ora_gl_init();
     return ora_truncnorm_impl(mu, sigma, lo, hi, u, &(int){0});
 }
 
@@ -600,6 +668,7 @@ int ora_run_from(const ora_problem *p, int chains, const double *f_start, long s
 {
     int N = p->N;
     long tot[4] = {0, 0, 0, 0};
+    ora_gl_init();
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #else

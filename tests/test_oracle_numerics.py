@@ -161,3 +161,34 @@ def test_jacobi_svd(m, n):
     for j in range(n):
         i = np.argmax(np.abs(V[:, j]))
         assert V[i, j] > 0
+
+
+def _exact_offset(a, w, u):
+    """t in [0, w] with int_0^t e^{-a s - s^2/2} = u int_0^w (80 digits)."""
+    a, w, u = mp.mpf(a), mp.mpf(w), mp.mpf(u)
+    r2 = mp.sqrt(2)
+    if a >= 0:   # erfc differences: no cancellation against 1 in the tails
+        I = lambda t: mp.exp(a * a / 2) * mp.sqrt(mp.pi / 2) * (mp.erfc(a / r2) - mp.erfc((a + t) / r2))
+    else:
+        I = lambda t: mp.exp(a * a / 2) * mp.sqrt(mp.pi / 2) * (mp.erfc(-(a + t) / r2) - mp.erfc(-a / r2))
+    tgt = u * I(w)
+    lo, hi = mp.mpf(0), w
+    for _ in range(300):
+        m = (lo + hi) / 2
+        lo, hi = (m, hi) if I(m) < tgt else (lo, m)
+    return (lo + hi) / 2
+
+
+@pytest.mark.parametrize("a", [-3.0, -0.2, 0.0, 0.3, 2.0, 10.0, 1e3, 1e6, -1e6])
+def test_truncnorm_narrow_intervals_keep_relative_accuracy(a):
+    """On intervals much narrower than sigma (weak modes), delta - lo must stay
+    accurate relative to hi - lo: lo = 0 and mu = -a put the interval at
+    [a, a + w] in standard units with delta = t exactly representable."""
+    for w in [1e-14, 1e-9, 1e-5, 1e-2, 0.3, 2.0]:
+        if w * (abs(a) + w) > 5.0:
+            continue
+        for u in [1e-9, 0.2, 0.5, 0.97]:
+            u = _grid(u)
+            t = O.truncnorm(-a, 1.0, 0.0, w, u)
+            e = _exact_offset(a, w, u)
+            assert abs(mp.mpf(t) - e) <= 64 * mp.mpf(2) ** -52 * w, (a, w, u, t, float(e))
