@@ -1,8 +1,10 @@
 """GPU parity of the CUDA sampler (through the C ABI) against the FP64 CPU oracle.
 
 * FP64 path, same singular vectors (the oracle's factors given to the library)
-  and the same Philox stream: chain states after every sweep agree with the
-  oracle's within 1e-9 relative (element by element).
+  and the same Philox stream: chain states after every sweep of a short run
+  agree with the oracle's within 1e-9 relative (element by element).  A short
+  run is the window over which the oracle reproduces itself from a start one
+  ulp away (the sampler's map amplifies rounding differences each sweep).
 * Invariants: fbar >= 0 after every sweep; the residual the kernel tracks
   incrementally equals |g~ - K~ f|^2 recomputed in FP64 within 1e-10 relative.
 * Long runs with the library's own factorisation (cuSOLVER): <fbar> agrees with
@@ -58,6 +60,22 @@ def _step_cases():
     yield "bosonic", W.small_problem(25, 70, seed=23, levels=[[0], [0, 20, 45]], bosonic=True)
 
 
+def _short_run_window(op, chains, sweeps, seed, f0):
+    """Sweeps over which FP64 trajectories are reproducible at all: the oracle
+    is run again from a start perturbed by one ulp, and the window ends at the
+    first sweep where its own two trajectories differ by more than 1e-11
+    (relative).  The Gibbs map of blocked modes sampling amplifies rounding
+    differences by ~1e2-1e4 per sweep, so later sweeps of two correct FP64
+    implementations differ by more than any fixed tolerance."""
+    a = op.run(chains, 0, sweeps, seed=seed, trace_chains=chains, f_start=f0)["trace"]
+    b = op.run(chains, 0, sweeps, seed=seed, trace_chains=chains, f_start=f0 * (1 + 2.0**-52))["trace"]
+    sens = (np.abs(a - b) / np.abs(a).max(axis=2, keepdims=True)).max(axis=(0, 2))
+    n = 0
+    while n < sweeps and sens[n] <= 1e-11:
+        n += 1
+    return max(n, 1), a
+
+
 @pytest.mark.parametrize("team", [32, 8])
 @pytest.mark.parametrize("case", list(range(4)))
 def test_fp64_matches_oracle_step_by_step(case, team):
@@ -65,15 +83,16 @@ def test_fp64_matches_oracle_step_by_step(case, team):
     op = O.OracleProblem(p.K, p.G, p.C, p.levels)
     dec = op.decomposition()
     chains, sweeps, seed = 7, 6, 1234 + case
-    ref = op.run(chains, 0, sweeps, seed=seed, trace_chains=chains)
+    window, ref = _short_run_window(op, chains, sweeps, seed, op.initial_f())
     gp = _gpu_problem(p, factors=dec, team=team)
     for s in range(sweeps):
         gp.sample(chains, 0, 1, seed, precision=asm.ASM_FP64, cont=s > 0)
         f, chi2 = gp.chain_state()
-        want = ref["trace"][:, s, :]
-        scale = np.abs(want).max(axis=1, keepdims=True)
-        err = np.abs(f - want) / scale
-        assert err.max() <= STEP_RTOL, (name, team, s, err.max())
+        if s < window:
+            want = ref[:, s, :]
+            err = np.abs(f - want) / np.abs(want).max(axis=1, keepdims=True)
+            assert err.max() <= STEP_RTOL, (name, team, s, err.max())
+        # invariants hold on every sweep: A >= 0 and the tracked residual
         assert f.min() >= 0.0
         exact = np.sum((dec.gt[None, :] - f @ dec.Kt.T) ** 2, axis=1)
         assert np.allclose(chi2, exact, rtol=CHI2_RTOL, atol=0), (name, s)
@@ -83,21 +102,28 @@ def test_fp64_matches_oracle_step_by_step(case, team):
 
 def test_fp64_full_size_sampled_chains():
     """The blocked-modes workload at full size (N=400, M=100, 1024 chains) in the
-    launch configuration of the benchmark: sampled chains match the oracle."""
+    launch configuration of the benchmark: sampled chains match the oracle over
+    the reproducible window (one sweep here)."""
     p = W.blocked_modes_problem()
     op = O.OracleProblem(p.K, p.G, p.C, p.levels)
     dec = op.decomposition()
-    chains, sweeps, seed = 1024, 3, 77
-    ref = op.run(chains, 0, sweeps, seed=seed, threads=0)
-    gp = _gpu_problem(p, factors=dec)
-    gp.sample(chains, 0, sweeps, seed, precision=asm.ASM_FP64)
-    f, chi2 = gp.chain_state()
+    chains, seed = 1024, 77
     idx = [0, 1, 333, 511, 512, 777, 1022, 1023]
+    ref = op.run(chains, 0, 1, seed=seed, threads=0)
+    gp = _gpu_problem(p, factors=dec)
+    gp.sample(chains, 0, 1, seed, precision=asm.ASM_FP64)
+    f, chi2 = gp.chain_state()
     want = ref["f_final"][idx]
     err = np.abs(f[idx] - want) / np.abs(want).max(axis=1, keepdims=True)
     assert err.max() <= STEP_RTOL, err.max()
     assert np.allclose(chi2[idx], ref["chi2"][idx], rtol=1e-9)
     assert f.min() >= 0.0
+    # and beyond the window the invariants still hold at full size
+    gp.sample(chains, 0, 20, seed, precision=asm.ASM_FP64, cont=True)
+    f, chi2 = gp.chain_state()
+    assert f.min() >= 0.0
+    exact = np.sum((dec.gt[None, :] - f[idx] @ dec.Kt.T) ** 2, axis=1)
+    assert np.allclose(chi2[idx], exact, rtol=CHI2_RTOL)
 
 
 def test_mixed_precision_tracks_fp64_over_one_sweep():
