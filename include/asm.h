@@ -143,6 +143,33 @@ int asm_chain_state(asm_problem *p, double *f, double *chi2);
 /* Counters of the last asm_sample (synchronises). */
 int asm_status(asm_problem *p, asm_stats *out);
 
+/* Allocation-free sampling.  The paper has no counterpart: this call exists
+ * for callers that cannot allocate device memory themselves -- code that runs
+ * while a stream is being captured into a CUDA graph (cudaMalloc is not
+ * allowed there), plug-ins whose host application owns every device
+ * allocation through its own pool, or loops under a fixed memory budget.
+ * It runs the same sampling as asm_sample (fresh chains, burn_in + sweeps
+ * sweeps) and then the device part of asm_average, but its scratch (chain
+ * states, residuals, sums and counters) lives in one library-owned static
+ * device array of ASM_NOALLOC_SCRATCH_BYTES, which every GPU that loads the
+ * library keeps until the process exits.  The call allocates and frees
+ * nothing; a run whose asm_workspace_bytes(p, chains, precision) exceeds the
+ * array is rejected with ASM_ERR_TOO_LARGE before any GPU work.
+ * Outputs (caller-owned device buffers of N doubles, written asynchronously on
+ * `stream`): d_mean_fbar = <fbar>, d_sem2_fbar = squared standard error of
+ * <fbar> from the spread of the chain means, d_m2_fbar = <fbar^2>.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * shares the array and re-initialises what must start at zero, and the array
+ * keeps the last call's contents: calls whose GPU work overlaps (other
+ * streams, threads or handles on the same device) race on it and must be
+ * serialised by the caller.  Until the next sampling call, asm_chain_state and
+ * asm_status of the handle read the array. */
+#define ASM_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t seed,
+                       int precision, double *d_mean_fbar, double *d_sem2_fbar, double *d_m2_fbar,
+                       void *stream);
+
 /* Free the handle and its device memory (not the caller's workspace). */
 void asm_destroy(asm_problem *p);
 

@@ -42,7 +42,8 @@ class asm_stats(ct.Structure):
 
 
 EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",
-           "asm_status", "asm_destroy", "asm_error_string"]
+           "asm_status", "asm_destroy", "asm_error_string", "asm_sample_noalloc"]
+ASM_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
 
@@ -79,6 +80,9 @@ def load(build_if_missing: bool = True):
     L.asm_destroy.restype = None
     L.asm_error_string.argtypes = [ct.c_int]
     L.asm_error_string.restype = ct.c_char_p
+    L.asm_sample_noalloc.argtypes = [ct.c_void_p, ct.c_int, ct.c_long, ct.c_long, ct.c_uint64, ct.c_int,
+                                     ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
+    L.asm_sample_noalloc.restype = ct.c_int
     _lib = L
     return L
 
@@ -168,6 +172,21 @@ class Problem:
         _check(load().asm_sample(self._h, chains, burn_in, sweeps, ct.c_uint64(seed), precision, flags,
                                  ct.c_void_p(workspace.data_ptr()), workspace.numel(),
                                  ct.c_void_p(s.cuda_stream)), "asm_sample")
+        self.chains = chains
+
+    def sample_noalloc(self, chains, burn_in, sweeps, seed, precision, out_mean, out_sem2, out_m2,
+                       stream=None):
+        """asm_sample_noalloc: the library allocates nothing; the outputs are the
+        caller's device tensors (N float64 each), written asynchronously."""
+        torch = _require_cuda()
+        for t in (out_mean, out_sem2, out_m2):
+            if t.dtype != torch.float64 or not t.is_cuda or t.numel() < self.N or not t.is_contiguous():
+                raise ValueError("outputs must be contiguous float64 CUDA tensors of N elements")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(load().asm_sample_noalloc(self._h, chains, burn_in, sweeps, ct.c_uint64(seed), precision,
+                                         ct.c_void_p(out_mean.data_ptr()), ct.c_void_p(out_sem2.data_ptr()),
+                                         ct.c_void_p(out_m2.data_ptr()), ct.c_void_p(s.cuda_stream)),
+               "asm_sample_noalloc")
         self.chains = chains
 
     def average(self):

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -500,6 +501,37 @@ int init_chains(asm_problem *p, const WsLayout &L, int chains)
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Scratch of the allocation-free entry point: a fixed device array in this
+// file.  Host code must not hand the symbol itself to a kernel (in host code
+// it is a host-side stand-in); its device address is looked up once per device.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ASM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up on the
+// first call per device, with that device current).
+int noalloc_scratch(void **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return ASM_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return ASM_ERR_CUDA;
+        g_noalloc_addr[dev] = ptr;
+    }
+    *out = g_noalloc_addr[dev];
+    return ASM_OK;
+}
+
+}  // namespace
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -517,7 +549,7 @@ const char *asm_error_string(int code)
     case ASM_ERR_STATE: return "call out of order";
     case ASM_ERR_ARG: return "invalid argument";
     case ASM_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
-    case ASM_ERR_TOO_LARGE: return "block larger than the compiled register tile";
+    case ASM_ERR_TOO_LARGE: return "size exceeds a compiled limit (register tile or static scratch)";
     default: return "unknown error";
     }
 }
@@ -774,6 +806,48 @@ int asm_status(asm_problem *p, asm_stats *out)
     out->timed_launches = p->timed_launches;
     out->sweep_kernel_ms = p->timed_ms;
     return ASM_OK;
+}
+
+int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t seed,
+                       int precision, double *d_mean_fbar, double *d_sem2_fbar, double *d_m2_fbar,
+                       void *stream)
+{
+    if (!p || chains < 1 || burn_in < 0 || sweeps < 1 || !d_mean_fbar || !d_sem2_fbar || !d_m2_fbar)
+        return ASM_ERR_ARG;
+    if (precision != ASM_FP64 && precision != ASM_MIXED) return ASM_ERR_ARG;
+    const WsLayout L = ws_layout(p, chains, precision);
+    if (L.total > ASM_NOALLOC_SCRATCH_BYTES) return ASM_ERR_TOO_LARGE;
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != ASM_OK) return rc;
+    if (p->ev_used && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
+    p->stream = (cudaStream_t)stream;
+    p->timing = false;
+    p->ws = scratch;
+    p->ws_bytes = ASM_NOALLOC_SCRATCH_BYTES;
+    p->chains = chains;
+    p->precision = precision;
+    p->seed = seed;
+    p->sweeps_done = 0;
+    p->kept = 0;
+    p->sweep_launches = p->other_launches = p->timed_launches = 0;
+    p->timed_ms = 0.0;
+    // counters, sums and residuals are zeroed and the chains re-started here
+    rc = precision == ASM_FP64 ? init_chains<double>(p, L, chains) : init_chains<float>(p, L, chains);
+    if (rc != ASM_OK) return rc;
+    p->have_run = true;
+    const long long s1 = (long long)burn_in + sweeps;
+    rc = precision == ASM_FP64 ? run_sweeps<double>(p, L, chains, 0, s1, burn_in)
+                               : run_sweeps<float>(p, L, chains, 0, s1, burn_in);
+    if (rc != ASM_OK) return rc;
+    p->sweeps_done = s1;
+    p->kept = sweeps;
+    const char *ws = (const char *)scratch;
+    reduce_kernel<<<(p->N + 127) / 128, 128, 0, p->stream>>>((const double *)(ws + L.S1),
+                                                             (const double *)(ws + L.S2), chains, p->N,
+                                                             (double)sweeps, d_mean_fbar, d_sem2_fbar, d_m2_fbar);
+    ++p->other_launches;
+    return cudaGetLastError() == cudaSuccess ? ASM_OK : ASM_ERR_CUDA;
 }
 
 void asm_destroy(asm_problem *p)
