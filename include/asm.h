@@ -42,7 +42,8 @@ enum {
     ASM_ERR_STATE = -6,      /* call out of order (e.g. average before sample) */
     ASM_ERR_ARG = -7,        /* NULL or out-of-range argument */
     ASM_ERR_WORKSPACE = -8,  /* workspace missing, too small or misaligned */
-    ASM_ERR_TOO_LARGE = -9   /* a block or level exceeds a compiled limit */
+    ASM_ERR_TOO_LARGE = -9,  /* a block or level exceeds a compiled limit */
+    ASM_ERR_TIMEOUT = -10    /* a bounded device wait gave up; the run's results are invalid */
 };
 
 enum { ASM_FP64 = 0, ASM_MIXED = 1 };   /* precision of asm_sample */
@@ -98,6 +99,7 @@ typedef struct {
     int64_t other_launches;     /* initial-state, refresh and reduction launches */
     int64_t timed_launches;     /* sweep launches timed with ASM_SAMPLE_TIMING */
     double sweep_kernel_ms;     /* summed event-timed duration of those launches */
+    int64_t timeouts;           /* bounded device waits that gave up (0 in a valid run) */
 } asm_stats;
 
 /* Set-up (Sec. IV: whitening C^{-1} = T^T T by Cholesky, K~ = T K, g~ = T G;
@@ -130,7 +132,8 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
                int precision, uint32_t flags, void *d_workspace, size_t workspace_bytes,
                void *stream);
 
-/* Results of the last asm_sample (synchronises).  Per grid point (N values,
+/* Results of the last asm_sample (synchronises; ASM_ERR_TIMEOUT if a bounded
+ * device wait of that run gave up).  Per grid point (N values,
  * any pointer may be NULL): mean_A = <fbar>/w, sem_A its standard error from
  * the spread of the independent chain means, ess = posterior variance of fbar
  * over sem^2, mean_fbar = <fbar>. */

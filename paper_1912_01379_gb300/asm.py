@@ -38,7 +38,8 @@ class asm_stats(ct.Structure):
                 ("zero_mode_moves", ct.c_int64), ("tail_capped", ct.c_int64),
                 ("nonfinite_moves", ct.c_int64), ("max_resync_drift", ct.c_double),
                 ("sweep_launches", ct.c_int64), ("other_launches", ct.c_int64),
-                ("timed_launches", ct.c_int64), ("sweep_kernel_ms", ct.c_double)]
+                ("timed_launches", ct.c_int64), ("sweep_kernel_ms", ct.c_double),
+                ("timeouts", ct.c_int64)]
 
 
 EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",

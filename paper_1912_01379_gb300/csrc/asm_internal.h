@@ -25,6 +25,9 @@ struct BlockDesc {
     long long offR;  // Rlo/Rhi base
     long long offd;  // d, invd: n values
     long long offU;  // Ut: np x M (mode-major); Um: M x np (grid-major)
+    long long offRec;  // move records of the block: n records of recstride elements
+    int recstride;     // elements per record (3 rs + 16 bytes, padded to 128 bytes)
+    int pad_;
 };
 
 // Device-side problem data in one precision T.
@@ -32,13 +35,16 @@ template <class T>
 struct ProblemData {
     const T *V, *Rlo, *Rhi;  // mode rows
     const T *d, *invd;       // singular values and their reciprocals (0 for zero modes)
+    const T *meta;           // per mode, 16 bytes: {d, 1/d} (FP32: {d, 1/d, 0, 0})
+    const T *rec;            // per move j: {V_j, Rlo_{j+1}, Rhi_{j+1} (rs each), meta_j}
     const T *Ut, *Um;        // U in two layouts
 };
 
 struct Counters {            // device counters, first bytes of the workspace
     unsigned long long degenerate, zero_mode, tail_capped, nonfinite;
     unsigned long long drift_bits;   // max relative chi2 drift, as ordered bits of a double
-    unsigned long long pad[3];
+    unsigned long long timeouts;     // bounded waits that gave up (the launch then stopped early)
+    unsigned long long pad[2];
 };
 
 template <class T>
@@ -58,11 +64,19 @@ struct SweepParams {
     Counters *counters;
     int cpad;                         // shared-memory stride of the c/w buffers (>= max np)
     int mpad;                         // shared-memory stride of the residual (>= M)
+    // move-record pipeline, shared by the CTA: `depth` stages filled by one
+    // producer warp with bulk copies (TMA engine); `full` barriers signal a
+    // landed record, `empty` barriers collect the consumer warps' releases
+    int depth;                        // stages in the ring
+    int consumers;                    // consumer warps per CTA (the producer is one more)
+    int off_full, off_empty, off_stages;  // byte offsets in dynamic shared memory
+    int stage_bytes;                  // bytes per stage (>= the largest record)
 };
 
 // Launchers (asm_sweep_f32.cu / asm_sweep_f64.cu).  kv: 16-byte vectors per lane.
-cudaError_t launch_sweeps_f32(const SweepParams<float> &p, int kv, int warps_per_cta, cudaStream_t s);
-cudaError_t launch_sweeps_f64(const SweepParams<double> &p, int kv, int warps_per_cta, cudaStream_t s);
+// The CTA has p.consumers consumer warps and one producer warp.
+cudaError_t launch_sweeps_f32(const SweepParams<float> &p, int kv, cudaStream_t s);
+cudaError_t launch_sweeps_f64(const SweepParams<double> &p, int kv, cudaStream_t s);
 // Largest supported kv per precision.
 constexpr int kMaxKvF32 = 16;   // 64 floats per lane
 constexpr int kMaxKvF64 = 32;   // 64 doubles per lane

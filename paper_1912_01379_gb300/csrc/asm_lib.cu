@@ -118,8 +118,8 @@ struct WsLayout {
 
 // device buffers of one precision
 struct PrecBuffers {
-    void *V = nullptr, *Rlo = nullptr, *Rhi = nullptr, *d = nullptr, *invd = nullptr, *Ut = nullptr,
-         *Um = nullptr;
+    void *V = nullptr, *Rlo = nullptr, *Rhi = nullptr, *d = nullptr, *invd = nullptr, *meta = nullptr,
+         *rec = nullptr, *Ut = nullptr, *Um = nullptr;
 };
 
 struct asm_problem {
@@ -129,7 +129,8 @@ struct asm_problem {
     std::vector<double> w;
     double f0 = 0.0;
     int max_nb = 0, max_np = 0;
-    long long totV = 0, totR = 0, totd = 0, totU = 0;
+    long long totV = 0, totR = 0, totd = 0, totU = 0, totRec = 0;
+    int max_rec = 0;   // largest record (elements)
     // device
     int *d_level_first = nullptr, *d_level_nblocks = nullptr;
     BlockDesc *d_blocks = nullptr;
@@ -182,7 +183,7 @@ int upload(void **dst, const std::vector<T> &src)
 
 void free_prec(PrecBuffers &b)
 {
-    void *ptrs[] = {b.V, b.Rlo, b.Rhi, b.d, b.invd, b.Ut, b.Um};
+    void *ptrs[] = {b.V, b.Rlo, b.Rhi, b.d, b.invd, b.meta, b.rec, b.Ut, b.Um};
     for (void *x : ptrs)
         if (x) cudaFree(x);
     b = PrecBuffers{};
@@ -328,8 +329,11 @@ int build_precision(asm_problem *p, const HostFactors &hf, PrecBuffers &out)
 {
     const int M = p->M;
     const T nan = std::numeric_limits<T>::quiet_NaN();
+    constexpr int MW = 16 / sizeof(T);
     std::vector<T> V(p->totV, T(0)), Rlo(p->totR, nan), Rhi(p->totR, nan), d(p->totd, T(0)),
-        invd(p->totd, T(0)), Ut(std::max<long long>(p->totU, 1), T(0)), Um(std::max<long long>(p->totU, 1), T(0));
+        invd(p->totd, T(0)), meta((size_t)p->totd * MW, T(0)), rec(std::max<long long>(p->totRec, 1), T(0)),
+        Ut(std::max<long long>(p->totU, 1), T(0)),
+        Um(std::max<long long>(p->totU, 1), T(0));
     for (int b = 0; b < p->n_blocks; ++b) {
         const BlockDesc &B = p->blocks[b];
         const std::vector<double> &hd = hf.d[b], &hV = hf.V[b], &hU = hf.U[b];
@@ -346,16 +350,30 @@ int build_precision(asm_problem *p, const HostFactors &hf, PrecBuffers &out)
             }
             d[B.offd + j] = (T)hd[j];
             invd[B.offd + j] = hd[j] > 0.0 ? (T)(1.0 / hd[j]) : T(0);
+            meta[(size_t)(B.offd + j) * MW] = d[B.offd + j];
+            meta[(size_t)(B.offd + j) * MW + 1] = invd[B.offd + j];
         }
         for (int j = 0; j < B.np; ++j)
             for (int m = 0; m < M; ++m) {
                 Ut[B.offU + (size_t)j * M + m] = (T)hU[(size_t)j * M + m];
                 Um[B.offU + (size_t)m * B.np + j] = (T)hU[(size_t)j * M + m];
             }
+        // move records: {V_j, Rlo_{j+1}, Rhi_{j+1}, d_j, 1/d_j}
+        for (int j = 0; j < B.n; ++j) {
+            T *r = &rec[B.offRec + (size_t)j * B.recstride];
+            for (int i = 0; i < B.rs; ++i) {
+                r[i] = V[B.offV + (size_t)j * B.rs + i];
+                r[B.rs + i] = Rlo[B.offR + (size_t)(j + 1) * B.rs + i];
+                r[2 * B.rs + i] = Rhi[B.offR + (size_t)(j + 1) * B.rs + i];
+            }
+            r[3 * B.rs] = d[B.offd + j];
+            r[3 * B.rs + 1] = invd[B.offd + j];
+        }
     }
     int rc;
     if ((rc = upload(&out.V, V)) || (rc = upload(&out.Rlo, Rlo)) || (rc = upload(&out.Rhi, Rhi)) ||
-        (rc = upload(&out.d, d)) || (rc = upload(&out.invd, invd)) || (rc = upload(&out.Ut, Ut)) ||
+        (rc = upload(&out.d, d)) || (rc = upload(&out.invd, invd)) || (rc = upload(&out.meta, meta)) || (rc = upload(&out.rec, rec)) ||
+        (rc = upload(&out.Ut, Ut)) ||
         (rc = upload(&out.Um, Um)))
         return rc;
     return ASM_OK;
@@ -428,7 +446,39 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.counters = (Counters *)(ws + L.counters);
     sp.cpad = round_up_int(std::max(p->max_np, 1), 32);
     sp.mpad = round_up_int(p->M, 32);
+    sp.pd.meta = (const T *)b.meta;
+    sp.pd.rec = (const T *)b.rec;
     return sp;
+}
+
+// Shared memory of the sweep kernel: per team c, w and r~; the ring's `full`
+// and `empty` barriers and `depth` record stages.  Consumer warps per CTA are
+// chosen so that the CTAs about cover the SMs once (all chains of an SM then
+// share one ring); the ring is as deep as the shared-memory budget allows.
+template <class T>
+bool plan_pipeline(SweepParams<T> &sp, int max_rec, int chains)
+{
+    constexpr int kSMs = 152;
+    const int TW = 32 / sp.S;
+    const long long warps = (chains + TW - 1) / TW;
+    int consumers = (int)std::min<long long>(8, std::max<long long>(1, (warps + kSMs - 1) / kSMs));
+    const long long ctas = (warps + consumers - 1) / consumers;
+    const int ctas_per_sm = (int)std::max<long long>(1, (ctas + kSMs - 1) / kSMs);
+    const size_t budget = std::min<size_t>(220 * 1024 / ctas_per_sm, 227 * 1024);
+    sp.stage_bytes = (int)align_up((size_t)max_rec * sizeof(T), 128);
+    auto fixed = [&](int c) {
+        return align_up((size_t)c * TW * (2 * sp.cpad + sp.mpad) * sizeof(T), 128) + 256;
+    };
+    int depth = 16;
+    while (depth > 2 && fixed(consumers) + (size_t)depth * sp.stage_bytes > budget) --depth;
+    while (consumers > 1 && fixed(consumers) + (size_t)depth * sp.stage_bytes > budget) --consumers;
+    if (fixed(consumers) + (size_t)depth * sp.stage_bytes > 227 * 1024) return false;
+    sp.consumers = consumers;
+    sp.depth = depth;
+    sp.off_full = (int)align_up((size_t)consumers * TW * (2 * sp.cpad + sp.mpad) * sizeof(T), 128);
+    sp.off_empty = sp.off_full + 128;
+    sp.off_stages = sp.off_full + 256;
+    return true;
 }
 
 int pick_kv(int max_nb, int vec, int S, int kmax)
@@ -449,6 +499,7 @@ int run_sweeps(asm_problem *p, const WsLayout &L, int chains, long long s_begin,
     const int vec = 16 / (int)sizeof(T);
     const int kv = pick_kv(p->max_nb, vec, sp.S, sizeof(T) == 8 ? kMaxKvF64 : kMaxKvF32);
     if (kv < 0) return ASM_ERR_TOO_LARGE;
+    if (!plan_pipeline(sp, p->max_rec, chains)) return ASM_ERR_TOO_LARGE;
     char *ws = (char *)p->ws;
     long long s = s_begin;
     while (s < s_end) {
@@ -463,8 +514,8 @@ int run_sweeps(asm_problem *p, const WsLayout &L, int chains, long long s_begin,
             if (!e0 || !e1 || cudaEventRecord(e0, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
         }
         cudaError_t e;
-        if constexpr (sizeof(T) == 8) e = launch_sweeps_f64(sp, kv, 4, p->stream);
-        else e = launch_sweeps_f32(sp, kv, 4, p->stream);
+        if constexpr (sizeof(T) == 8) e = launch_sweeps_f64(sp, kv, p->stream);
+        else e = launch_sweeps_f32(sp, kv, p->stream);
         if (e != cudaSuccess) return ASM_ERR_CUDA;
         if (p->timing && cudaEventRecord(e1, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
         ++p->sweep_launches;
@@ -550,6 +601,7 @@ const char *asm_error_string(int code)
     case ASM_ERR_ARG: return "invalid argument";
     case ASM_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
     case ASM_ERR_TOO_LARGE: return "size exceeds a compiled limit (register tile or static scratch)";
+    case ASM_ERR_TIMEOUT: return "a bounded device wait gave up; results of that run are invalid";
     default: return "unknown error";
     }
 }
@@ -575,7 +627,7 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
         nb += ds->level_nblocks[l];
     }
     p->n_blocks = nb;
-    long long oV = 0, oR = 0, od = 0, oU = 0;
+    long long oV = 0, oR = 0, od = 0, oU = 0, oRec = 0;
     for (int l = 0; l < ds->n_levels; ++l) {
         const int *st = ds->block_start + p->level_first[l];
         for (int b = 0; b < ds->level_nblocks[l]; ++b) {
@@ -590,12 +642,15 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
             B.offR = oR; oR += (long long)(B.n + 1) * B.rs;
             B.offd = od; od += B.n;
             B.offU = oU; oU += (long long)B.np * M;
+            B.recstride = 3 * B.rs + 16;   // elements; 16 holds the mode data in both precisions
+            B.offRec = oRec; oRec += (long long)B.n * B.recstride;
+            p->max_rec = std::max(p->max_rec, B.recstride);
             p->blocks.push_back(B);
             p->max_nb = std::max(p->max_nb, B.n);
             p->max_np = std::max(p->max_np, B.np);
         }
     }
-    p->totV = oV; p->totR = oR; p->totd = od; p->totU = oU;
+    p->totV = oV; p->totR = oR; p->totd = od; p->totU = oU; p->totRec = oRec;
     p->w.assign(N, 1.0);
     if (ds->w) {
         if (!all_finite(ds->w, N)) { delete p; return ASM_ERR_NONFINITE; }
@@ -718,10 +773,27 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
     return ASM_OK;
 }
 
+namespace {
+// Reads the run's device counters (synchronises the stream).
+int read_counters(asm_problem *p, Counters *c)
+{
+    if (cudaMemcpyAsync(c, p->ws, sizeof(*c), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    return ASM_OK;
+}
+}  // namespace
+
 int asm_average(asm_problem *p, double *mean_A, double *sem_A, double *ess, double *mean_fbar)
 {
     if (!p) return ASM_ERR_ARG;
     if (!p->have_run || p->kept < 1) return ASM_ERR_STATE;
+    {
+        Counters c{};
+        const int rc0 = read_counters(p, &c);
+        if (rc0 != ASM_OK) return rc0;
+        if (c.timeouts) return ASM_ERR_TIMEOUT;
+    }
     const WsLayout L = ws_layout(p, p->chains, p->precision);
     const int N = p->N;
     double *d = nullptr;
@@ -753,6 +825,12 @@ int asm_chain_state(asm_problem *p, double *f, double *chi2)
 {
     if (!p) return ASM_ERR_ARG;
     if (!p->have_run) return ASM_ERR_STATE;
+    {
+        Counters c{};
+        const int rc0 = read_counters(p, &c);
+        if (rc0 != ASM_OK) return rc0;
+        if (c.timeouts) return ASM_ERR_TIMEOUT;
+    }
     const WsLayout L = ws_layout(p, p->chains, p->precision);
     const size_t es = p->precision == ASM_FP64 ? 8 : 4;
     const char *ws = (const char *)p->ws;
@@ -805,6 +883,7 @@ int asm_status(asm_problem *p, asm_stats *out)
     out->other_launches = p->other_launches;
     out->timed_launches = p->timed_launches;
     out->sweep_kernel_ms = p->timed_ms;
+    out->timeouts = (int64_t)c.timeouts;
     return ASM_OK;
 }
 

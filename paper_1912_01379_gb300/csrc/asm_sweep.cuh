@@ -296,29 +296,273 @@ __device__ __forceinline__ T shfl_xor(T v, int off)
 }
 
 // --------------------------------------------------------------------------
-// the sweep kernel: sweeps [sweep0, sweep0 + nsweeps) of every chain
+// bulk copies (TMA engine) and mbarriers, inline PTX
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after `limit` polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int limit)
+{
+    for (int i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+constexpr int kWaitLimit = 1 << 22;
+
+// Team-wide max of lo and min of hi.  FP32: one redux instruction each on
+// integer keys that order like the floats (neither value is ever NaN).
+// FP64: a butterfly of shuffles.
+__device__ __forceinline__ int ord_key(float f)
+{
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord_val(int k)
+{
+    return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff);
+}
+__device__ __forceinline__ void team_bounds(float &lo, float &hi, int S, int team_base)
+{
+    const unsigned mask = S == 32 ? 0xffffffffu : (((1u << S) - 1u) << team_base);
+    lo = ord_val(__reduce_max_sync(mask, ord_key(lo)));
+    hi = ord_val(__reduce_min_sync(mask, ord_key(hi)));
+}
+__device__ __forceinline__ void team_bounds(double &lo, double &hi, int S, int)
+{
+    for (int off = 1; off < S; off <<= 1) {
+        lo = fmax(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = fmin(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+}
+
+// 16-byte vector loads from shared memory
+__device__ __forceinline__ void lds_v(const float *p, float (&o)[4])
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void lds_v(const double *p, double (&o)[2])
+{
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    o[0] = v.x; o[1] = v.y;
+}
+
+// f += delta * V (clamped at 0) and the bounds of the next mode, rows read
+// from a shared-memory stage.
+template <class T, int KV>
+__device__ __forceinline__ void fused_pass_smem(T (&f)[KV][VecOf<T>::n], T delta, const T *vrow,
+                                                const T *rlrow, const T *rhrow, int kcnt, int sl, int S,
+                                                T &lo, T &hi)
+{
+    constexpr int VEC = VecOf<T>::n;
+    T la[VEC], ha[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+        la[v] = -CUDART_INF_F;
+        ha[v] = CUDART_INF_F;
+    }
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+        if (k < kcnt) {
+            const int idx = VEC * (k * S + sl);
+            T vv[VEC], rl[VEC], rh[VEC];
+            lds_v(vrow + idx, vv);
+            lds_v(rlrow + idx, rl);
+            lds_v(rhrow + idx, rh);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                T x = m_fma(delta, vv[v], f[k][v]);
+                x = m_max(x, T(0));
+                f[k][v] = x;
+                la[v] = m_max(la[v], x * rl[v]);
+                ha[v] = m_min(ha[v], x * rh[v]);
+            }
+        }
+    }
+    lo = la[0];
+    hi = ha[0];
+#pragma unroll
+    for (int v = 1; v < VEC; ++v) {
+        lo = m_max(lo, la[v]);
+        hi = m_min(hi, ha[v]);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Position in the stream of moves of a launch (sweep, level, block, mode).
+// --------------------------------------------------------------------------
+struct MoveCursor {
+    long long s;            // sweep
+    int bi, j;              // block within the level, mode within the block
+    int nb;                 // blocks of the level
+    const BlockDesc *bd;    // blocks of the level
+    BlockDesc B;            // the current block (a copy)
+    bool done;
+};
+
+__device__ __forceinline__ int level_of_sweep(long long s, unsigned long long seed, unsigned long long pid,
+                                              int n_levels)
+{
+    unsigned long long l0 = ~0ull, l1 = (unsigned long long)s, l2 = 0ull, l3 = pid;
+    philox4x64_10(l0, l1, l2, l3, seed, 0ull);
+    int level = (int)(uniform_from<double>(l0) * n_levels);
+    return level >= n_levels ? n_levels - 1 : level;
+}
+
+template <class T>
+__device__ __forceinline__ void cursor_start_sweep(MoveCursor &c, const SweepParams<T> &p)
+{
+    const int level = level_of_sweep(c.s, p.seed, p.problem_id, p.n_levels);
+    c.nb = p.level_nblocks[level];
+    c.bd = p.blocks + p.level_first[level];
+    c.bi = 0;
+    c.j = 0;
+    c.B = c.bd[0];
+}
+
+template <class T>
+__device__ __forceinline__ void cursor_advance(MoveCursor &c, const SweepParams<T> &p)
+{
+    if (++c.j < c.B.n) return;
+    c.j = 0;
+    if (++c.bi < c.nb) {
+        c.B = c.bd[c.bi];
+        return;
+    }
+    if (++c.s >= p.sweep0 + p.nsweeps) {
+        c.done = true;
+        return;
+    }
+    cursor_start_sweep(c, p);
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// --------------------------------------------------------------------------
+// The producer warp: one bulk copy per move of the launch into the ring,
+// after every consumer warp has released the slot's previous record.
+// --------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void produce(const SweepParams<T> &p, unsigned long long *full,
+                                        unsigned long long *empty, unsigned char *stages, Counters *cnt)
+{
+    if ((threadIdx.x & 31) != 0 || p.nsweeps <= 0) return;
+    const int D = p.depth;
+    MoveCursor c;
+    c.s = p.sweep0;
+    c.done = false;
+    cursor_start_sweep(c, p);
+    unsigned long long g = 0;
+    bool failed = false;
+    for (; !c.done; ++g) {
+        const int slot = (int)(g % (unsigned long long)D);
+        if (g >= (unsigned long long)D) {
+            const unsigned parity = (unsigned)(((g / (unsigned long long)D) - 1ull) & 1ull);
+            if (!mbar_wait(empty + slot, parity, kWaitLimit)) {
+                failed = true;
+                break;
+            }
+        }
+        const unsigned bytes = (unsigned)(c.B.recstride * sizeof(T));
+        mbar_expect_tx(full + slot, bytes);
+        bulk_g2s(stages + (size_t)slot * p.stage_bytes, p.pd.rec + c.B.offRec + (size_t)c.j * c.B.recstride,
+                 bytes, full + slot);
+        cursor_advance(c, p);
+    }
+    if (failed) {
+        // the copies already issued must land before the CTA may exit
+        for (unsigned long long k = g > (unsigned long long)D ? g - D : 0; k < g; ++k)
+            mbar_wait(full + (k % (unsigned long long)D), (unsigned)((k / (unsigned long long)D) & 1ull),
+                      kWaitLimit);
+        atomicAdd(&cnt->timeouts, 1ull);
+    }
+}
+
+// --------------------------------------------------------------------------
+// the sweep kernel: sweeps [sweep0, sweep0 + nsweeps) of every chain.
+// Warps 0 .. consumers-1 run chains; warp `consumers` produces the records.
 // --------------------------------------------------------------------------
 template <class T, int KV>
-__global__ void __launch_bounds__(128) sweep_kernel(const SweepParams<T> p)
+__global__ void __launch_bounds__(288) sweep_kernel(const SweepParams<T> p)
 {
     constexpr int VEC = VecOf<T>::n;
     const int lane = threadIdx.x & 31;
     const int wcta = threadIdx.x >> 5;
+    const int D = p.depth;
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem_raw + p.off_full);
+    unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem_raw + p.off_empty);
+    unsigned char *stages = smem_raw + p.off_stages;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < D; ++i) {
+            mbar_init(full + i, 1);
+            mbar_init(empty + i, (unsigned)p.consumers);
+        }
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    if (wcta == p.consumers) {
+        produce(p, full, empty, stages, p.counters);
+        return;
+    }
+
     const int S = p.S;
     const int TW = 32 / S;
     const int team = lane / S;
     const int sl = lane - team * S;
     const int team_base = team * S;
-    const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + wcta;
+    const long long gwarp = (long long)blockIdx.x * p.consumers + wcta;
     const long long q_raw = gwarp * TW + team;
     const bool active = q_raw < p.chains;
     const long long q = active ? q_raw : (long long)p.chains - 1;  // idle teams shadow a real chain, write nothing
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *csm = reinterpret_cast<T *>(smem_raw) + (size_t)(wcta * TW + team) * (2 * p.cpad + p.mpad);
     T *wsm = csm + p.cpad;
     T *rsm = wsm + p.cpad;
-
     T *Rq = p.R + (size_t)q * p.ldR;
     for (int m = sl; m < p.M; m += S) rsm[m] = Rq[m];
     T *Fq = p.F + (size_t)q * p.ldF;
@@ -330,19 +574,18 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepParams<T> p)
     unsigned long long n_deg = 0, n_zero = 0, n_bad = 0;
     int capped = 0;
     unsigned long long rw0 = 0, rw1 = 0, rw2 = 0, rw3 = 0;
+    unsigned long long g = 0;   // move sequence number (warp-uniform)
+    bool failed = false;
 
-    for (long long s = p.sweep0; s < p.sweep0 + p.nsweeps; ++s) {
+    for (long long s = p.sweep0; s < p.sweep0 + p.nsweeps && !failed; ++s) {
         // level of this sweep: same for every chain of the problem (Sec. IV.C)
-        unsigned long long l0 = ~0ull, l1 = (unsigned long long)s, l2 = 0ull, l3 = p.problem_id;
-        philox4x64_10(l0, l1, l2, l3, p.seed, 0ull);
-        int level = (int)(uniform_from<double>(l0) * p.n_levels);
-        if (level >= p.n_levels) level = p.n_levels - 1;
+        const int level = level_of_sweep(s, p.seed, p.problem_id, p.n_levels);
         const bool keep = s >= p.burn_in;
         long long win = -1;  // first move index covered by this lane's Philox words
         const int nb = p.level_nblocks[level];
         const BlockDesc *bd = p.blocks + p.level_first[level];
 
-        for (int bi = 0; bi < nb; ++bi) {
+        for (int bi = 0; bi < nb && !failed; ++bi) {
             const BlockDesc B = bd[bi];
             const int kcnt = (B.n + VEC * S - 1) / (VEC * S);
             // entry: the block's f into registers
@@ -353,27 +596,28 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepParams<T> p)
                     const int nl = VEC * (k * S + sl) + v;
                     f[k][v] = (k < kcnt && nl < B.n) ? Fq[B.start + nl] : T(0);
                 }
-            // c = U_b^T r~ (lanes split the modes)
+            // c = U_b^T r~ (lanes split the modes; four partial sums per mode)
             const T *Um = p.pd.Um + B.offU;
             for (int j = sl; j < B.np; j += S) {
-                T a = T(0);
-                for (int m = 0; m < p.M; ++m) a = m_fma(__ldg(Um + (size_t)m * B.np + j), rsm[m], a);
-                csm[j] = a;
+                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+                int m = 0;
+                for (; m + 3 < p.M; m += 4) {
+                    a0 = m_fma(__ldg(Um + (size_t)m * B.np + j), rsm[m], a0);
+                    a1 = m_fma(__ldg(Um + (size_t)(m + 1) * B.np + j), rsm[m + 1], a1);
+                    a2 = m_fma(__ldg(Um + (size_t)(m + 2) * B.np + j), rsm[m + 2], a2);
+                    a3 = m_fma(__ldg(Um + (size_t)(m + 3) * B.np + j), rsm[m + 3], a3);
+                }
+                for (; m < p.M; ++m) a0 = m_fma(__ldg(Um + (size_t)m * B.np + j), rsm[m], a0);
+                csm[j] = (a0 + a1) + (a2 + a3);
             }
             __syncwarp();
 
-            const T *Vb = p.pd.V + B.offV;
-            const T *Rl = p.pd.Rlo + B.offR;
-            const T *Rh = p.pd.Rhi + B.offR;
-            const T *db = p.pd.d + B.offd;
-            const T *idb = p.pd.invd + B.offd;
             T lo, hi;
-            fused_pass<T, KV>(f, T(0), Vb, Rl, Rh, kcnt, sl, S, lo, hi);  // bounds of mode 0
+            fused_pass<T, KV>(f, T(0), p.pd.V + B.offV, p.pd.Rlo + B.offR, p.pd.Rhi + B.offR, kcnt, sl, S,
+                              lo, hi);  // bounds of mode 0
             for (int j = 0; j < B.n; ++j) {
-                for (int off = 1; off < S; off <<= 1) {
-                    lo = m_max(lo, shfl_xor(lo, off));
-                    hi = m_min(hi, shfl_xor(hi, off));
-                }
+                // what does not depend on the bounds first: c_j and the uniform
+                const T cj = j < B.np ? csm[j] : T(0);
                 // uniform of move t: word t%4 of Philox(ctr = {t/4, s, q, problem})
                 const int t = B.start + j;
                 if (win < 0 || t >= win + 4 * S) {
@@ -389,8 +633,18 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepParams<T> p)
                 const int src = (t >> 2) - (int)(win >> 2);
                 const unsigned long long word = __shfl_sync(0xffffffffu, mine, team_base + src);
                 const T u = uniform_from<T>(word);
+                // this move's record
+                const int slot = (int)(g % (unsigned long long)D);
+                const unsigned parity = (unsigned)((g / (unsigned long long)D) & 1ull);
+                const bool ok = mbar_wait(full + slot, parity, kWaitLimit);
+                if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
+                    failed = true;
+                    break;
+                }
+                const T *st = reinterpret_cast<const T *>(stages + (size_t)slot * p.stage_bytes);
+                const T dj = st[3 * B.rs], ij = st[3 * B.rs + 1];
 
-                const T dj = __ldg(db + j);
+                team_bounds(lo, hi, S, team_base);
                 T delta;
                 if (!(hi > lo)) {
                     delta = T(0);
@@ -399,23 +653,34 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepParams<T> p)
                     delta = m_fma(u, hi - lo, lo);
                     ++n_zero;
                 } else {
-                    delta = tn_step<T>(csm[j], dj, __ldg(idb + j), lo, hi, u, capped);
+                    delta = tn_step<T>(cj, dj, ij, lo, hi, u, capped);
                 }
                 if (!isfinite(delta)) {
                     delta = T(0);
                     ++n_bad;
                 }
                 if (j < B.np && sl == 0) wsm[j] = dj * delta;
-                fused_pass<T, KV>(f, delta, Vb + (size_t)j * B.rs, Rl + (size_t)(j + 1) * B.rs,
-                                  Rh + (size_t)(j + 1) * B.rs, kcnt, sl, S, lo, hi);
+                fused_pass_smem<T, KV>(f, delta, st, st + B.rs, st + 2 * B.rs, kcnt, sl, S, lo, hi);
+                // release the record to the producer (one arrival per warp)
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty + slot);
+                ++g;
             }
+            if (failed) break;
             __syncwarp();
-            // exit: r~ -= U_b w (lanes split the data points)
+            // exit: r~ -= U_b w (lanes split the data points; four partial sums)
             const T *Ut = p.pd.Ut + B.offU;
             for (int m = sl; m < p.M; m += S) {
-                T a = T(0);
-                for (int j = 0; j < B.np; ++j) a = m_fma(__ldg(Ut + (size_t)j * p.M + m), wsm[j], a);
-                rsm[m] -= a;
+                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+                int j = 0;
+                for (; j + 3 < B.np; j += 4) {
+                    a0 = m_fma(__ldg(Ut + (size_t)j * p.M + m), wsm[j], a0);
+                    a1 = m_fma(__ldg(Ut + (size_t)(j + 1) * p.M + m), wsm[j + 1], a1);
+                    a2 = m_fma(__ldg(Ut + (size_t)(j + 2) * p.M + m), wsm[j + 2], a2);
+                    a3 = m_fma(__ldg(Ut + (size_t)(j + 3) * p.M + m), wsm[j + 3], a3);
+                }
+                for (; j < B.np; ++j) a0 = m_fma(__ldg(Ut + (size_t)j * p.M + m), wsm[j], a0);
+                rsm[m] -= (a0 + a1) + (a2 + a3);
             }
             // write the block back and accumulate the kept sweep
 #pragma unroll
@@ -436,6 +701,10 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepParams<T> p)
             __syncwarp();
         }
     }
+    if (failed) {
+        if (lane == 0) atomicAdd(&p.counters->timeouts, 1ull);
+        return;
+    }
     if (active) {
         for (int m = sl; m < p.M; m += S) Rq[m] = rsm[m];
         if (sl == 0) {
@@ -448,16 +717,16 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepParams<T> p)
 }
 
 template <class T, int KV>
-cudaError_t launch_sweep_kernel(const SweepParams<T> &p, int warps_per_cta, cudaStream_t stream)
+cudaError_t launch_sweep_kernel(const SweepParams<T> &p, cudaStream_t stream)
 {
     const int TW = 32 / p.S;
     const long long warps = (p.chains + TW - 1) / TW;
-    const long long ctas = (warps + warps_per_cta - 1) / warps_per_cta;
-    const size_t smem = (size_t)warps_per_cta * TW * (2 * p.cpad + p.mpad) * sizeof(T);
+    const long long ctas = (warps + p.consumers - 1) / p.consumers;
+    const size_t smem = (size_t)p.off_stages + (size_t)p.depth * p.stage_bytes;
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    sweep_kernel<T, KV><<<(unsigned)ctas, 32 * warps_per_cta, smem, stream>>>(p);
+    sweep_kernel<T, KV><<<(unsigned)ctas, 32 * (p.consumers + 1), smem, stream>>>(p);
     return cudaGetLastError();
 }
 

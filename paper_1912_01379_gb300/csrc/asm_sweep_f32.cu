@@ -3,14 +3,14 @@
 
 namespace asmgb {
 
-cudaError_t launch_sweeps_f32(const SweepParams<float> &p, int kv, int warps_per_cta, cudaStream_t s)
+cudaError_t launch_sweeps_f32(const SweepParams<float> &p, int kv, cudaStream_t s)
 {
     switch (kv) {
-    case 1: return launch_sweep_kernel<float, 1>(p, warps_per_cta, s);
-    case 2: return launch_sweep_kernel<float, 2>(p, warps_per_cta, s);
-    case 4: return launch_sweep_kernel<float, 4>(p, warps_per_cta, s);
-    case 8: return launch_sweep_kernel<float, 8>(p, warps_per_cta, s);
-    case 16: return launch_sweep_kernel<float, 16>(p, warps_per_cta, s);
+    case 1: return launch_sweep_kernel<float, 1>(p, s);
+    case 2: return launch_sweep_kernel<float, 2>(p, s);
+    case 4: return launch_sweep_kernel<float, 4>(p, s);
+    case 8: return launch_sweep_kernel<float, 8>(p, s);
+    case 16: return launch_sweep_kernel<float, 16>(p, s);
     default: return cudaErrorInvalidValue;
     }
 }
