@@ -462,6 +462,10 @@ bool plan_pipeline(SweepParams<T> &sp, int max_rec, int chains)
     const int TW = 32 / sp.S;
     const long long warps = (chains + TW - 1) / TW;
     int consumers = (int)std::min<long long>(8, std::max<long long>(1, (warps + kSMs - 1) / kSMs));
+    if (const char *e = std::getenv("ASM_CONSUMERS_PER_CTA")) {   // tuning override
+        const int c = std::atoi(e);
+        if (c >= 1 && c <= 8) consumers = c;
+    }
     const long long ctas = (warps + consumers - 1) / consumers;
     const int ctas_per_sm = (int)std::max<long long>(1, (ctas + kSMs - 1) / kSMs);
     const size_t budget = std::min<size_t>(220 * 1024 / ctas_per_sm, 227 * 1024);
@@ -470,6 +474,10 @@ bool plan_pipeline(SweepParams<T> &sp, int max_rec, int chains)
         return align_up((size_t)c * TW * (2 * sp.cpad + sp.mpad) * sizeof(T), 128) + 256;
     };
     int depth = 16;
+    if (const char *e = std::getenv("ASM_RING_DEPTH")) {            // tuning override
+        const int d = std::atoi(e);
+        if (d >= 2 && d <= 16) depth = d;
+    }
     while (depth > 2 && fixed(consumers) + (size_t)depth * sp.stage_bytes > budget) --depth;
     while (consumers > 1 && fixed(consumers) + (size_t)depth * sp.stage_bytes > budget) --consumers;
     if (fixed(consumers) + (size_t)depth * sp.stage_bytes > 227 * 1024) return false;

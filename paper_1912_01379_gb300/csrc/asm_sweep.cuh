@@ -323,12 +323,31 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait: gives up after `limit` polls (each poll may suspend briefly).
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int limit)
 {
     for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+// Consumer-side wait: a non-blocking test first (the record has usually
+// landed long before it is needed), then the suspending wait, bounded.
+__device__ __forceinline__ bool mbar_wait_ready(unsigned long long *bar, unsigned parity, int limit)
+{
+    if (mbar_test_wait(bar, parity)) return true;
+    return mbar_wait(bar, parity, limit);
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
 {
@@ -636,7 +655,7 @@ __global__ void __launch_bounds__(288) sweep_kernel(const SweepParams<T> p)
                 // this move's record
                 const int slot = (int)(g % (unsigned long long)D);
                 const unsigned parity = (unsigned)((g / (unsigned long long)D) & 1ull);
-                const bool ok = mbar_wait(full + slot, parity, kWaitLimit);
+                const bool ok = mbar_wait_ready(full + slot, parity, kWaitLimit);
                 if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
                     failed = true;
                     break;
