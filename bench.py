@@ -31,6 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1912_01379_gb300 import replicas  # noqa: E402
 from paper_1912_01379_gb300 import workloads as W  # noqa: E402
 
 METRIC = "chain-mode updates/s and ESS/s of <A(omega)>: mixed-prec vs plain FP64, 1 GB300"
@@ -142,6 +143,22 @@ def _ops_per_level(p):
     return np.array(ops, dtype=np.float64)
 
 
+def _captured_traffic():
+    """DRAM bytes per sweep-kernel launch from the committed ncu summary of this
+    workload, or None when the kernel source has changed since that capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "sweep_kernel_f32_blocked_modes.md")
+    src = os.path.join(ROOT, "paper_1912_01379_gb300", "csrc", "asm_sweep.cuh")
+    try:
+        fields = dict(l.split(":", 1) for l in open(prof).read().splitlines() if ":" in l and " " not in l.split(":")[0])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if fields.get("kernel_source_sha256", "").strip() == sha:
+            return int(fields["dram_bytes_per_launch"].strip())
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def _peaks():
     try:
         with open(PEAKS) as fh:
@@ -211,9 +228,11 @@ def main():
     p = W.blocked_modes_problem(chains=args.chains)
     gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w)
     chains, burn, sweeps = args.chains, args.burn, args.sweeps
+    # replicas: every rank samples its own `chains` chains, keyed by global chain id
+    gp.set_stream_ids(0, rank * chains)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    seed_base = 1000 + 7919 * rank           # replicas: independent chains per rank
+    seed_base = 1000
 
     # warm-up (untimed), full steps
     for w in range(args.warmup):
@@ -244,6 +263,8 @@ def main():
         sweep_launches += st["timed_launches"]
         other_launches += st["other_launches"]
         r = gp.average()
+        if ws > 1:   # the one exchange of the replicas: FP64 sums across ranks
+            r = replicas.combine(replicas.partial_from_average(r["mean_fbar"], r["sem_fbar"], r["ess"], chains))
         ess_min.append(float(np.nanmin(r["ess"])))
         lv = _level_sequence(seed, burn + sweeps, len(p.levels))
         ops_total += chains * float(np.sum(ops_lvl[lv]))
@@ -320,7 +341,8 @@ def main():
             "fp64": fp64,
             "speedup_vs_fp64": (value / ws) / fp64["updates_per_s"] if fp64 else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-op/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None, "traffic": _captured_traffic(),
+                         "traffic_unit": "DRAM bytes per launch (ncu capture, profiles/)",
                          "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({src} sm_max_mhz)",
                          "kernel": "sweep_kernel<float>", "avg_launch_ms": sweep_ms / max(sweep_launches, 1)},
             "cpu_baseline": cpu,

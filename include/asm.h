@@ -118,7 +118,8 @@ size_t asm_workspace_bytes(const asm_problem *p, int chains, int precision);
  * once, blocks left to right, modes in index order).  Each move draws the step
  * along its mode from the exact 1-D conditional, a Gaussian truncated to the
  * interval of Eq. modeLimits (flat for zero modes), by the inverse CDF of one
- * Philox4x64-10 uniform keyed by (seed, problem 0, chain, sweep, move).
+ * Philox4x64-10 uniform keyed by (seed, problem id, global chain id, sweep,
+ * move); see asm_set_stream_ids.
  * Sweeps after burn-in are accumulated into FP64 sums of fbar and fbar^2.
  * precision: ASM_FP64 runs the chain state in FP64; ASM_MIXED runs it in FP32
  * with FP64 accumulators and an FP64 residual refresh every 64 sweeps.
@@ -172,6 +173,28 @@ int asm_status(asm_problem *p, asm_stats *out);
 int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t seed,
                        int precision, double *d_mean_fbar, double *d_sem2_fbar, double *d_m2_fbar,
                        void *stream);
+
+/* Identities that key the random numbers (Philox counter words): problem_id
+ * (default 0) and the global id of local chain 0 (default 0).  Chains are
+ * independent and keyed by their global id, so shards of one run placed on
+ * several GPUs with chain_offset = first global chain of the shard reproduce
+ * the unsharded run chain by chain (multi-GPU replicas: each GPU samples its
+ * shard; the FP64 sums are added on the host).  Takes effect at the next
+ * asm_sample that starts fresh chains. */
+int asm_set_stream_ids(asm_problem *p, uint64_t problem_id, uint64_t chain_offset);
+
+/* Checkpoint of the run state (synchronises): chain states, tracked residuals,
+ * sums, counters and the sweep count, so that a restored run continues bit for
+ * bit.  host_buf NULL: *bytes receives the size needed.  Otherwise *bytes is
+ * the buffer size on input and the bytes written on output. */
+int asm_checkpoint(asm_problem *p, void *host_buf, size_t *bytes);
+
+/* Restore a checkpoint into d_workspace (>= asm_workspace_bytes for the
+ * checkpoint's chains and precision) of a handle set up for the same problem;
+ * the next asm_sample with ASM_SAMPLE_CONTINUE (same chains, seed, precision,
+ * workspace) continues the run.  Synchronises `stream`. */
+int asm_restore(asm_problem *p, const void *host_buf, size_t bytes, void *d_workspace,
+                size_t workspace_bytes, void *stream);
 
 /* Free the handle and its device memory (not the caller's workspace). */
 void asm_destroy(asm_problem *p);

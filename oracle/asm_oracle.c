@@ -602,7 +602,7 @@ int ora_conditional(const ora_problem *p, int level, int block, int j, const dou
     return 0;
 }
 
-static void ora_chain(const ora_problem *p, int q, double *f, long sweep0, long burn_in,
+static void ora_chain(const ora_problem *p, uint64_t q, double *f, long sweep0, long burn_in,
                       long sweeps, uint64_t seed, uint64_t problem_id, double *S1, double *S2,
                       double *trace, long *stats)
 {
@@ -661,10 +661,10 @@ static void ora_chain(const ora_problem *p, int q, double *f, long sweep0, long 
     free(gp); free(h);
 }
 
-int ora_run_from(const ora_problem *p, int chains, const double *f_start, long sweep0,
-                 long burn_in, long sweeps, uint64_t seed, uint64_t problem_id, int n_threads,
-                 double *f_final, double *S1, double *S2, double *chi2_final,
-                 double *trace, int n_traced, long *stats)
+int ora_run_ids(const ora_problem *p, int chains, const double *f_start, long sweep0,
+                long burn_in, long sweeps, uint64_t seed, uint64_t problem_id, uint64_t chain0,
+                int n_threads, double *f_final, double *S1, double *S2, double *chi2_final,
+                double *trace, int n_traced, long *stats)
 {
     int N = p->N;
     long tot[4] = {0, 0, 0, 0};
@@ -687,7 +687,7 @@ int ora_run_from(const ora_problem *p, int chains, const double *f_start, long s
             memset(s1, 0, sizeof(double) * N);
             memset(s2, 0, sizeof(double) * N);
             double *tr = (trace && q < n_traced) ? trace + (size_t)q * (burn_in + sweeps) * N : NULL;
-            ora_chain(p, q, f, sweep0, burn_in, sweeps, seed, problem_id, s1, s2, tr, st);
+            ora_chain(p, chain0 + (uint64_t)q, f, sweep0, burn_in, sweeps, seed, problem_id, s1, s2, tr, st);
             if (f_final) memcpy(f_final + (size_t)q * N, f, sizeof(double) * N);
             if (S1) memcpy(S1 + (size_t)q * N, s1, sizeof(double) * N);
             if (S2) memcpy(S2 + (size_t)q * N, s2, sizeof(double) * N);
@@ -700,6 +700,15 @@ int ora_run_from(const ora_problem *p, int chains, const double *f_start, long s
     }
     if (stats) for (int k = 0; k < 4; ++k) stats[k] = tot[k];
     return 0;
+}
+
+int ora_run_from(const ora_problem *p, int chains, const double *f_start, long sweep0,
+                 long burn_in, long sweeps, uint64_t seed, uint64_t problem_id, int n_threads,
+                 double *f_final, double *S1, double *S2, double *chi2_final,
+                 double *trace, int n_traced, long *stats)
+{
+    return ora_run_ids(p, chains, f_start, sweep0, burn_in, sweeps, seed, problem_id, 0, n_threads,
+                       f_final, S1, S2, chi2_final, trace, n_traced, stats);
 }
 
 int ora_run(const ora_problem *p, int chains, long burn_in, long sweeps, uint64_t seed,

@@ -92,6 +92,13 @@ int ora_run_from(const ora_problem *p, int chains, const double *f_start, long s
                  double *f_final, double *S1, double *S2, double *chi2_final,
                  double *trace, int n_traced, long *stats);
 
+/* Same, with the global id of local chain 0 (chain q uses id chain0 + q in
+ * its random-number counters): shards of a run reproduce the whole run. */
+int ora_run_ids(const ora_problem *p, int chains, const double *f_start, long sweep0,
+                long burn_in, long sweeps, uint64_t seed, uint64_t problem_id, uint64_t chain0,
+                int n_threads, double *f_final, double *S1, double *S2, double *chi2_final,
+                double *trace, int n_traced, long *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,10 @@ def lib():
                                    ct.c_uint64, ct.c_uint64, ct.c_int, _dp, _dp, _dp, _dp, _dp,
                                    ct.c_int, _lp]
         L.ora_run_from.restype = ct.c_int
+        L.ora_run_ids.argtypes = [ct.c_void_p, ct.c_int, _dp, ct.c_long, ct.c_long, ct.c_long,
+                                  ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_int, _dp, _dp, _dp, _dp, _dp,
+                                  ct.c_int, _lp]
+        L.ora_run_ids.restype = ct.c_int
         _lib = L
     return _lib
 
@@ -197,7 +201,7 @@ class OracleProblem:
         return mu.value, sg.value, lo.value, hi.value
 
     def run(self, chains, burn_in, sweeps, seed, problem_id=0, threads=0, trace_chains=0,
-            f_start=None, sweep0=0):
+            f_start=None, sweep0=0, chain_offset=0):
         """Returns a dict with f_final, S1, S2 (chains x N), chi2 (chains),
         kept (sweeps), stats and, if asked, trace (trace_chains x sweeps_total x N)."""
         N = self.N
@@ -209,14 +213,11 @@ class OracleProblem:
         trace = np.zeros((trace_chains, total, N)) if trace_chains else None
         stats = np.zeros(4, dtype=np.int64)
         if f_start is None:
-            rc = lib().ora_run(self._h, chains, burn_in, sweeps, ct.c_uint64(seed), ct.c_uint64(problem_id),
-                               threads, _d(f_final), _d(S1), _d(S2), _d(chi2), _d(trace), trace_chains,
-                               stats.ctypes.data_as(_lp))
-        else:
-            fs = np.ascontiguousarray(np.broadcast_to(f_start, (chains, N)), dtype=np.float64)
-            rc = lib().ora_run_from(self._h, chains, _d(fs), sweep0, burn_in, sweeps, ct.c_uint64(seed),
-                                    ct.c_uint64(problem_id), threads, _d(f_final), _d(S1), _d(S2),
-                                    _d(chi2), _d(trace), trace_chains, stats.ctypes.data_as(_lp))
+            f_start = self.initial_f()
+        fs = np.ascontiguousarray(np.broadcast_to(f_start, (chains, N)), dtype=np.float64)
+        rc = lib().ora_run_ids(self._h, chains, _d(fs), sweep0, burn_in, sweeps, ct.c_uint64(seed),
+                               ct.c_uint64(problem_id), ct.c_uint64(chain_offset), threads, _d(f_final),
+                               _d(S1), _d(S2), _d(chi2), _d(trace), trace_chains, stats.ctypes.data_as(_lp))
         if rc != 0:
             raise RuntimeError("oracle run failed")
         return {"f_final": f_final, "S1": S1, "S2": S2, "chi2": chi2, "kept": sweeps,

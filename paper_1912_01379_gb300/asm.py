@@ -43,7 +43,8 @@ class asm_stats(ct.Structure):
 
 
 EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",
-           "asm_status", "asm_destroy", "asm_error_string", "asm_sample_noalloc"]
+           "asm_status", "asm_destroy", "asm_error_string", "asm_sample_noalloc", "asm_set_stream_ids",
+           "asm_checkpoint", "asm_restore"]
 ASM_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
@@ -84,6 +85,12 @@ def load(build_if_missing: bool = True):
     L.asm_sample_noalloc.argtypes = [ct.c_void_p, ct.c_int, ct.c_long, ct.c_long, ct.c_uint64, ct.c_int,
                                      ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
     L.asm_sample_noalloc.restype = ct.c_int
+    L.asm_set_stream_ids.argtypes = [ct.c_void_p, ct.c_uint64, ct.c_uint64]
+    L.asm_set_stream_ids.restype = ct.c_int
+    L.asm_checkpoint.argtypes = [ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_size_t)]
+    L.asm_checkpoint.restype = ct.c_int
+    L.asm_restore.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_size_t, ct.c_void_p]
+    L.asm_restore.restype = ct.c_int
     _lib = L
     return L
 
@@ -203,6 +210,28 @@ class Problem:
         chi2 = np.zeros(self.chains)
         _check(load().asm_chain_state(self._h, _dptr(f), _dptr(chi2)), "asm_chain_state")
         return f, chi2
+
+    def set_stream_ids(self, problem_id=0, chain_offset=0):
+        _check(load().asm_set_stream_ids(self._h, ct.c_uint64(problem_id), ct.c_uint64(chain_offset)),
+               "asm_set_stream_ids")
+
+    def checkpoint(self) -> bytes:
+        n = ct.c_size_t(0)
+        _check(load().asm_checkpoint(self._h, None, ct.byref(n)), "asm_checkpoint")
+        buf = ct.create_string_buffer(n.value)
+        _check(load().asm_checkpoint(self._h, buf, ct.byref(n)), "asm_checkpoint")
+        return buf.raw[:n.value]
+
+    def restore(self, blob: bytes, chains, precision=ASM_MIXED, stream=None):
+        torch = _require_cuda()
+        need = self.workspace_bytes(chains, precision)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        buf = ct.create_string_buffer(blob, len(blob))
+        _check(load().asm_restore(self._h, buf, len(blob), ct.c_void_p(self._ws.data_ptr()), self._ws.numel(),
+                                  ct.c_void_p(s.cuda_stream)), "asm_restore")
+        self.chains = chains
 
     def status(self):
         st = asm_stats()

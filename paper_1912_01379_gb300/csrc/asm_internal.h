@@ -61,6 +61,7 @@ struct SweepParams {
     int chains;
     long long sweep0, nsweeps, burn_in;
     unsigned long long seed, problem_id;
+    unsigned long long chain_offset;  // global id of local chain 0 (Philox key word)
     Counters *counters;
     int cpad;                         // shared-memory stride of the c/w buffers (>= max np)
     int mpad;                         // shared-memory stride of the residual (>= M)

@@ -142,6 +142,8 @@ struct asm_problem {
     int chains = 0, precision = -1, team = 32;
     long long sweeps_done = 0, kept = 0;
     unsigned long long seed = 0;
+    unsigned long long problem_id = 0, chain_offset = 0;   // Philox identities of the run
+    unsigned long long next_problem_id = 0, next_chain_offset = 0;
     cudaStream_t stream = nullptr;
     bool have_run = false;
     // launch bookkeeping
@@ -442,7 +444,8 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.S2 = (double *)(ws + L.S2);
     sp.chains = chains;
     sp.seed = p->seed;
-    sp.problem_id = 0;
+    sp.problem_id = p->problem_id;
+    sp.chain_offset = p->chain_offset;
     sp.counters = (Counters *)(ws + L.counters);
     sp.cpad = round_up_int(std::max(p->max_np, 1), 32);
     sp.mpad = round_up_int(p->M, 32);
@@ -764,6 +767,8 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
         p->chains = chains;
         p->precision = precision;
         p->seed = seed;
+        p->problem_id = p->next_problem_id;
+        p->chain_offset = p->next_chain_offset;
         p->sweeps_done = 0;
         p->kept = 0;
         p->sweep_launches = p->other_launches = p->timed_launches = 0;
@@ -915,6 +920,8 @@ int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, ui
     p->chains = chains;
     p->precision = precision;
     p->seed = seed;
+    p->problem_id = p->next_problem_id;
+    p->chain_offset = p->next_chain_offset;
     p->sweeps_done = 0;
     p->kept = 0;
     p->sweep_launches = p->other_launches = p->timed_launches = 0;
@@ -935,6 +942,80 @@ int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, ui
                                                              (double)sweeps, d_mean_fbar, d_sem2_fbar, d_m2_fbar);
     ++p->other_launches;
     return cudaGetLastError() == cudaSuccess ? ASM_OK : ASM_ERR_CUDA;
+}
+
+int asm_set_stream_ids(asm_problem *p, uint64_t problem_id, uint64_t chain_offset)
+{
+    if (!p) return ASM_ERR_ARG;
+    p->next_problem_id = problem_id;
+    p->next_chain_offset = chain_offset;
+    return ASM_OK;
+}
+
+namespace {
+struct CheckpointHeader {
+    uint64_t magic, version;
+    int64_t M, N, chains, precision;
+    uint64_t seed, problem_id, chain_offset;
+    int64_t sweeps_done, kept, ws_bytes;
+};
+constexpr uint64_t kCheckpointMagic = 0x41534d434b505431ull;   // "ASMCKPT1"
+}  // namespace
+
+int asm_checkpoint(asm_problem *p, void *host_buf, size_t *bytes)
+{
+    if (!p || !bytes) return ASM_ERR_ARG;
+    if (!p->have_run) return ASM_ERR_STATE;
+    const WsLayout L = ws_layout(p, p->chains, p->precision);
+    const size_t need = sizeof(CheckpointHeader) + L.total;
+    if (!host_buf) {
+        *bytes = need;
+        return ASM_OK;
+    }
+    if (*bytes < need) return ASM_ERR_ARG;
+    CheckpointHeader h{kCheckpointMagic, 1, p->M, p->N, p->chains, p->precision, p->seed, p->problem_id,
+                       p->chain_offset, p->sweeps_done, p->kept, (int64_t)L.total};
+    std::memcpy(host_buf, &h, sizeof(h));
+    if (cudaMemcpyAsync((char *)host_buf + sizeof(h), p->ws, L.total, cudaMemcpyDeviceToHost, p->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    *bytes = need;
+    return ASM_OK;
+}
+
+int asm_restore(asm_problem *p, const void *host_buf, size_t bytes, void *d_workspace, size_t workspace_bytes,
+                void *stream)
+{
+    if (!p || !host_buf || bytes < sizeof(CheckpointHeader)) return ASM_ERR_ARG;
+    CheckpointHeader h;
+    std::memcpy(&h, host_buf, sizeof(h));
+    if (h.magic != kCheckpointMagic || h.version != 1) return ASM_ERR_ARG;
+    if (h.M != p->M || h.N != p->N) return ASM_ERR_SHAPE;
+    if (h.precision != ASM_FP64 && h.precision != ASM_MIXED) return ASM_ERR_ARG;
+    const WsLayout L = ws_layout(p, (int)h.chains, (int)h.precision);
+    if ((int64_t)L.total != h.ws_bytes || bytes < sizeof(h) + L.total) return ASM_ERR_ARG;
+    if (!d_workspace || workspace_bytes < L.total || ((uintptr_t)d_workspace & 255)) return ASM_ERR_WORKSPACE;
+    if (p->ev_used && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
+    p->stream = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(d_workspace, (const char *)host_buf + sizeof(h), L.total, cudaMemcpyHostToDevice,
+                        p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    p->ws = d_workspace;
+    p->ws_bytes = workspace_bytes;
+    p->chains = (int)h.chains;
+    p->precision = (int)h.precision;
+    p->seed = h.seed;
+    p->problem_id = p->next_problem_id = h.problem_id;
+    p->chain_offset = p->next_chain_offset = h.chain_offset;
+    p->sweeps_done = h.sweeps_done;
+    p->kept = h.kept;
+    p->sweep_launches = p->other_launches = p->timed_launches = 0;
+    p->timed_ms = 0.0;
+    p->timing = false;
+    p->have_run = true;
+    return ASM_OK;
 }
 
 void asm_destroy(asm_problem *p)

@@ -642,8 +642,8 @@ __global__ void __launch_bounds__(288) sweep_kernel(const SweepParams<T> p)
                 if (win < 0 || t >= win + 4 * S) {
                     win = (long long)(t / (4 * S)) * (4 * S);
                     unsigned long long c0 = (unsigned long long)(win >> 2) + (unsigned long long)sl;
-                    unsigned long long c1 = (unsigned long long)s, c2 = (unsigned long long)q,
-                                       c3 = p.problem_id;
+                    unsigned long long c1 = (unsigned long long)s,
+                                       c2 = (unsigned long long)q + p.chain_offset, c3 = p.problem_id;
                     philox4x64_10(c0, c1, c2, c3, p.seed, 0ull);
                     rw0 = c0; rw1 = c1; rw2 = c2; rw3 = c3;
                 }

@@ -193,3 +193,38 @@ def test_edge_cases_and_errors():
     small = torch.empty(64, dtype=torch.uint8, device="cuda")
     with pytest.raises(asm.ASMError, match="workspace"):
         gp.sample(4, 0, 1, 1, workspace=small)
+
+
+def test_shards_reproduce_the_unsharded_run_chain_by_chain():
+    """Replicas: chains keyed by global id, so two shards equal one run."""
+    p = W.small_problem(16, 40, seed=9, levels=[[0], [0, 13, 29]])
+    whole = _gpu_problem(p)
+    whole.sample(20, 5, 30, 77, precision=asm.ASM_MIXED)
+    fw, _ = whole.chain_state()
+    parts = []
+    for off, n in [(0, 12), (12, 8)]:
+        gp = _gpu_problem(p)
+        gp.set_stream_ids(0, off)
+        gp.sample(n, 5, 30, 77, precision=asm.ASM_MIXED)
+        parts.append(gp.chain_state()[0])
+    assert np.array_equal(np.concatenate(parts), fw)
+
+
+@pytest.mark.parametrize("precision", [asm.ASM_FP64, asm.ASM_MIXED])
+def test_checkpoint_restore_continues_bit_for_bit(precision):
+    p = W.small_problem(16, 40, seed=10, levels=[[0], [0, 13, 29]])
+    ref = _gpu_problem(p)
+    ref.sample(9, 10, 130, 5, precision=precision)          # crosses a refresh boundary
+    f_ref, chi_ref = ref.chain_state()
+    avg_ref = ref.average()
+    a = _gpu_problem(p)
+    a.sample(9, 10, 50, 5, precision=precision)
+    blob = a.checkpoint()
+    del a
+    b = _gpu_problem(p)
+    b.restore(blob, 9, precision=precision)
+    b.sample(9, 0, 80, 5, precision=precision, cont=True)
+    f_b, chi_b = b.chain_state()
+    assert np.array_equal(f_b, f_ref)
+    assert np.array_equal(chi_b, chi_ref)
+    assert np.array_equal(b.average()["mean_fbar"], avg_ref["mean_fbar"])
