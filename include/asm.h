@@ -51,6 +51,8 @@ enum { ASM_FP64 = 0, ASM_MIXED = 1 };   /* precision of asm_sample */
 /* asm_sample flags */
 #define ASM_SAMPLE_CONTINUE 1u   /* keep the chains of the previous call and go on */
 #define ASM_SAMPLE_TIMING 2u     /* record CUDA events around every sweep-kernel launch */
+#define ASM_SAMPLE_MOMENTS 4u    /* accumulate the snapshot moments asm_backward needs */
+#define ASM_SNAPSHOT_EVERY 8     /* kept sweeps between snapshots of all chains */
 
 typedef struct asm_problem asm_problem;  /* opaque, library-owned */
 
@@ -72,8 +74,12 @@ typedef struct asm_problem asm_problem;  /* opaque, library-owned */
  *                after block in level order, d (n_b singular values, 0 marks a
  *                zero mode), V (n_b x n_b, mode-major: V[j*n_b+i] = component i
  *                of mode j) and U (min(M,n_b) x M, mode-major).  K, G, C are then
- *                unused.  This reproduces another implementation's modes.
- *  flags         reserved, 0. */
+ *                unused unless C is also given, which the G-gradient of
+ *                asm_backward needs.  This reproduces another implementation's modes.
+ *  flags         reserved, 0.
+ *  P, dK_dtheta, dw_dtheta  optional derivatives of the kernel and of the
+ *                weights with respect to P grid-density (default-model)
+ *                parameters; asm_backward then also returns the theta-gradient. */
 typedef struct {
     int M, N;
     const double *K;
@@ -85,6 +91,9 @@ typedef struct {
     const int *block_start;
     const double *Kt, *gt, *d, *V, *U;
     uint32_t flags;
+    int P;                      /* number of grid-density parameters theta (0: none) */
+    const double *dK_dtheta;    /* P x M x N: dK/dtheta_p (row-major per p), or NULL */
+    const double *dw_dtheta;    /* P x N: dw/dtheta_p, or NULL */
 } asm_desc;
 
 /* Counters of the last asm_sample run (asm_status). */
@@ -139,6 +148,20 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
  * the spread of the independent chain means, ess = posterior variance of fbar
  * over sem^2, mean_fbar = <fbar>. */
 int asm_average(asm_problem *p, double *mean_A, double *sem_A, double *ess, double *mean_fbar);
+
+/* Vector-Jacobian products of <A> = <fbar>/w (synchronises; needs a run with
+ * ASM_SAMPLE_MOMENTS).  With v (N) the cotangent of <A>:
+ *  grad_G (M)      = v^T d<A>/dG = C^{-1} K Cov(fbar, fbar) (v/w): the derivative of
+ *                    the posterior mean under exp(-chi^2/2) (Eq. likelihood) is the
+ *                    posterior covariance with the gradient of -chi^2/2, which is
+ *                    C^{-1}(K fbar - G), linear in fbar.
+ *  grad_theta (P)  = Cov((v/w)^T fbar, s_p) - sum_n v_n <fbar_n> dw_n/dtheta_p / w_n^2,
+ *                    s_p = (G - K fbar)^T C^{-1} (dK/dtheta_p) fbar (the flat measure on
+ *                    fbar does not depend on theta).
+ * Moments come from snapshots of all chains every ASM_SNAPSHOT_EVERY kept sweeps.
+ * grad_G needs the covariance C (computed or given at set-up); grad_theta needs
+ * P > 0; either pointer may be NULL. */
+int asm_backward(asm_problem *p, const double *v, double *grad_G, double *grad_theta);
 
 /* Current chain states (synchronises): f (chains x N, FP64 copy of fbar) and
  * chi2 (chains) = |r~|^2 of the residual the sampler tracks; either may be NULL. */

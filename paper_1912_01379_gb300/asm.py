@@ -19,6 +19,8 @@ ASM_FP64 = 0
 ASM_MIXED = 1
 ASM_SAMPLE_CONTINUE = 1
 ASM_SAMPLE_TIMING = 2
+ASM_SAMPLE_MOMENTS = 4
+ASM_SNAPSHOT_EVERY = 8
 
 _dp = ct.POINTER(ct.c_double)
 _ip = ct.POINTER(ct.c_int)
@@ -29,7 +31,7 @@ class asm_desc(ct.Structure):
                 ("K", _dp), ("G", _dp), ("C", _dp), ("w", _dp),
                 ("n_levels", ct.c_int), ("level_nblocks", _ip), ("block_start", _ip),
                 ("Kt", _dp), ("gt", _dp), ("d", _dp), ("V", _dp), ("U", _dp),
-                ("flags", ct.c_uint32)]
+                ("flags", ct.c_uint32), ("P", ct.c_int), ("dK_dtheta", _dp), ("dw_dtheta", _dp)]
 
 
 class asm_stats(ct.Structure):
@@ -44,7 +46,7 @@ class asm_stats(ct.Structure):
 
 EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",
            "asm_status", "asm_destroy", "asm_error_string", "asm_sample_noalloc", "asm_set_stream_ids",
-           "asm_checkpoint", "asm_restore"]
+           "asm_checkpoint", "asm_restore", "asm_backward"]
 ASM_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
@@ -91,6 +93,8 @@ def load(build_if_missing: bool = True):
     L.asm_checkpoint.restype = ct.c_int
     L.asm_restore.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_size_t, ct.c_void_p]
     L.asm_restore.restype = ct.c_int
+    L.asm_backward.argtypes = [ct.c_void_p, _dp, _dp, _dp]
+    L.asm_backward.restype = ct.c_int
     _lib = L
     return L
 
@@ -125,7 +129,7 @@ class Problem:
     weights (A = fbar / w).  `factors` (optional) is an object with Kt, gt, d,
     V, U arrays in the layout of asm_desc to use given singular vectors."""
 
-    def __init__(self, K, G, C, levels, w=None, factors=None):
+    def __init__(self, K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None):
         L = load()
         self._keep = []
         K = np.ascontiguousarray(K, dtype=np.float64)
@@ -147,6 +151,14 @@ class Problem:
             arrs = [np.ascontiguousarray(getattr(factors, k), dtype=np.float64) for k in ("Kt", "gt", "d", "V", "U")]
             self._keep += arrs
             d.Kt, d.gt, d.d, d.V, d.U = (_dptr(a) for a in arrs)
+        self.P = 0
+        if dK_dtheta is not None:
+            dK = np.ascontiguousarray(dK_dtheta, dtype=np.float64)
+            dw = np.ascontiguousarray(dw_dtheta, dtype=np.float64)
+            self.P = dK.shape[0]
+            assert dK.shape == (self.P, self.M, self.N) and dw.shape == (self.P, self.N)
+            self._keep += [dK, dw]
+            d.P, d.dK_dtheta, d.dw_dtheta = self.P, _dptr(dK), _dptr(dw)
         h = ct.c_void_p()
         _check(L.asm_setup(ct.byref(d), ct.byref(h)), "asm_setup")
         self._h = h
@@ -162,7 +174,7 @@ class Problem:
         return int(load().asm_workspace_bytes(self._h, chains, precision))
 
     def sample(self, chains, burn_in, sweeps, seed, precision=ASM_MIXED, cont=False, stream=None,
-               workspace=None, timing=False):
+               workspace=None, timing=False, moments=False):
         """asm_sample on a torch workspace (allocated here unless given) and the
         current torch stream (or `stream`)."""
         torch = _require_cuda()
@@ -176,7 +188,8 @@ class Problem:
         else:
             self._ws = workspace
         s = stream if stream is not None else torch.cuda.current_stream()
-        flags = (ASM_SAMPLE_CONTINUE if cont else 0) | (ASM_SAMPLE_TIMING if timing else 0)
+        flags = ((ASM_SAMPLE_CONTINUE if cont else 0) | (ASM_SAMPLE_TIMING if timing else 0) |
+                 (ASM_SAMPLE_MOMENTS if moments else 0))
         _check(load().asm_sample(self._h, chains, burn_in, sweeps, ct.c_uint64(seed), precision, flags,
                                  ct.c_void_p(workspace.data_ptr()), workspace.numel(),
                                  ct.c_void_p(s.cuda_stream)), "asm_sample")
@@ -204,6 +217,15 @@ class Problem:
                "asm_average")
         return {"mean_A": mean_A, "sem_A": sem_A, "ess": ess, "mean_fbar": mean_f,
                 "sem_fbar": sem_A * self.w}
+
+    def backward(self, v, want_G=True, want_theta=None):
+        """asm_backward: vector-Jacobian products of <A> for the cotangent v (N)."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        want_theta = self.P > 0 if want_theta is None else want_theta
+        gG = np.zeros(self.M) if want_G else None
+        gt = np.zeros(self.P) if want_theta else None
+        _check(load().asm_backward(self._h, _dptr(v), _dptr(gG), _dptr(gt)), "asm_backward")
+        return gG, gt
 
     def chain_state(self):
         f = np.zeros((self.chains, self.N))

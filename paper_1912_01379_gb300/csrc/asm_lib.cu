@@ -104,13 +104,133 @@ __global__ void reduce_kernel(const double *S1, const double *S2, int chains, in
 }
 
 // ---------------------------------------------------------------------------
+// snapshot moments for the backward pass
+// ---------------------------------------------------------------------------
+// Sf[n] += sum over chains of f[q][n]
+template <class T>
+__global__ void colsum_kernel(const T *F, int ldF, int chains, int N, double *Sf)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double a = 0.0;
+    for (int q = 0; q < chains; ++q) a += (double)F[(size_t)q * ldF + n];
+    Sf[n] += a;
+}
+
+__global__ void add_f32_to_f64(const float *x, double *y, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] += (double)x[i];
+}
+
+// shift[n] = mean over chains of f[q][n] (the centre of all later snapshots)
+template <class T>
+__global__ void shift_kernel(const T *F, int ldF, int chains, int N, double *shift)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double a = 0.0;
+    for (int q = 0; q < chains; ++q) a += (double)F[(size_t)q * ldF + n];
+    shift[n] = a / chains;
+}
+
+// D = F - shift (rows of chains, padding kept at zero)
+template <class T>
+__global__ void center_kernel(const T *F, int ldF, int chains, int N, const double *shift, T *D)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)chains * ldF) return;
+    const int n = (int)(i % ldF);
+    D[i] = n < N ? (T)((double)F[i] - shift[n]) : T(0);
+}
+
+// kshift[p*M + m] = (K~_theta_p shift)[m] in FP64
+__global__ void kshift_kernel(const double *Kth, const double *shift, int M, int N, int P, double *kshift)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * P) return;
+    const int pi = i / M, m = i - pi * M;
+    double a = 0.0;
+    for (int n = 0; n < N; ++n) a += Kth[((size_t)pi * M + m) * N + n] * shift[n];
+    kshift[i] = a;
+}
+
+// Scores of parameter p: s[q] = r~_q . (Y[:, q] + kshift_p) with Y = K~_theta_p D^T
+// (M x chains, column-major) of the centred snapshot; one warp per chain, FP64.
+template <class T>
+__global__ void score_kernel(const T *R, int ldR, const T *Y, const double *kshift, int M, int chains, int P,
+                             int pi, double *Sq)
+{
+    const long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= chains) return;
+    double a = 0.0;
+    for (int m = lane; m < M; m += 32)
+        a += (double)R[(size_t)q * ldR + m] * ((double)Y[(size_t)q * M + m] + kshift[(size_t)pi * M + m]);
+    for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+    if (lane == 0) Sq[(size_t)q * P + pi] = a;
+}
+
+// Sfs[n*P + p] += sum_q f[q][n] s[q][p]; Ss[p] += sum_q s[q][p] (thread n < P also does Ss).
+template <class T>
+__global__ void fs_kernel(const T *F, int ldF, const double *Sq, int chains, int N, int P, double *Sfs,
+                          double *Ss)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    for (int pi = 0; pi < P; ++pi) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < chains; ++q) {
+            const double s = Sq[(size_t)q * P + pi];
+            a += (double)F[(size_t)q * ldF + n] * s;
+            b += s;
+        }
+        Sfs[(size_t)n * P + pi] += a;
+        if (n == 0) Ss[pi] += b;
+    }
+}
+
+// Backward: u = Cov(fbar) v' from the snapshot moments (v' = v / w).
+// (the moments are of d = fbar - shift: the covariance is unchanged)
+__global__ void vjp_cov_kernel(const double *Sff, const double *Sf, double ns, const double *vp, int N, double *u)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double mv = 0.0, a = 0.0;
+    for (int k = 0; k < N; ++k) {
+        mv += Sf[k] * vp[k];
+        a += Sff[(size_t)k * N + n] * vp[k];
+    }
+    u[n] = a / ns - (Sf[n] / ns) * (mv / ns);
+}
+
+// Backward: g_theta[p] = Cov(v'^T fbar, s_p) - sum_n v_n <fbar_n> dw_pn / w_n^2.
+__global__ void vjp_theta_kernel(const double *Sfs, const double *Ss, const double *Sf, const double *shift,
+                                 double ns, const double *vp, const double *v, const double *w, const double *dw,
+                                 int N, int P, double *g)
+{
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= P) return;
+    double c = 0.0, m = 0.0, t = 0.0;
+    for (int n = 0; n < N; ++n) {
+        c += vp[n] * Sfs[(size_t)n * P + pi];
+        m += vp[n] * Sf[n];
+        t += v[n] * (Sf[n] / ns + shift[n]) * dw[(size_t)pi * N + n] / (w[n] * w[n]);
+    }
+    g[pi] = c / ns - (m / ns) * (Ss[pi] / ns) - t;
+}
+
+// ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 int round_up_int(int x, int a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
-    size_t counters, F, R, S1, S2, chi2, total;
+    size_t counters, F, R, S1, S2, chi2;
+    size_t Sff, Sf, Sfs, Ss, Gtmp, Y, Sq;   // snapshot moments for the backward pass
+    size_t shift, kshift, D;                // centring of the snapshots
+    size_t total;
     int ldF, ldR;
 };
 
@@ -135,6 +255,16 @@ struct asm_problem {
     int *d_level_first = nullptr, *d_level_nblocks = nullptr;
     BlockDesc *d_blocks = nullptr;
     double *d_KtT = nullptr, *d_gt = nullptr;
+    // backward pass
+    int P = 0;
+    double *d_L = nullptr;                 // Cholesky factor of C (M x M, column-major lower)
+    double *d_Kth64 = nullptr;             // whitened dK/dtheta, P x M x N
+    float *d_Kth32 = nullptr;
+    double *d_w = nullptr, *d_dw = nullptr;   // weights and dw/dtheta (P x N)
+    double *d_vjp = nullptr;               // scratch of asm_backward: v', v, u (N each), y (M), g (P)
+    cublasHandle_t blas = nullptr;
+    bool moments = false;
+    long long nsnap = 0;                   // chain snapshots in the moments
     PrecBuffers b64, b32;
     // run state
     void *ws = nullptr;
@@ -169,6 +299,17 @@ WsLayout ws_layout(const asm_problem *p, int chains, int precision)
     L.S1 = off; off = align_up(off + (size_t)chains * p->N * 8, 256);
     L.S2 = off; off = align_up(off + (size_t)chains * p->N * 8, 256);
     L.chi2 = off; off = align_up(off + (size_t)chains * 8, 256);
+    const size_t N = (size_t)p->N, P = (size_t)p->P;
+    L.Sff = off; off = align_up(off + N * N * 8, 256);
+    L.Sf = off; off = align_up(off + N * 8, 256);
+    L.Sfs = off; off = align_up(off + N * std::max<size_t>(P, 1) * 8, 256);
+    L.Ss = off; off = align_up(off + std::max<size_t>(P, 1) * 8, 256);
+    L.Gtmp = off; off = align_up(off + (precision == ASM_FP64 ? 0 : N * N * 4), 256);
+    L.Y = off; off = align_up(off + (P ? (size_t)chains * p->M * es : 0), 256);
+    L.Sq = off; off = align_up(off + (size_t)chains * std::max<size_t>(P, 1) * 8, 256);
+    L.shift = off; off = align_up(off + N * 8, 256);
+    L.kshift = off; off = align_up(off + (size_t)p->M * std::max<size_t>(P, 1) * 8, 256);
+    L.D = off; off = align_up(off + (size_t)chains * L.ldF * es, 256);
     L.total = off;
     return L;
 }
@@ -206,7 +347,7 @@ struct HostFactors {
 
 // Whitening (C = L L^T, K~ = L^{-1} K, g~ = L^{-1} G) and the SVD of every block,
 // all in FP64 on the device (cuSOLVER potrf / gesvd, cuBLAS trsm / trsv).
-int device_factorize(const asm_desc *ds, const asm_problem *p, HostFactors &hf)
+int device_factorize(const asm_desc *ds, const asm_problem *p, HostFactors &hf, double **L_out)
 {
     const int M = ds->M, N = ds->N;
     int rc = ASM_OK;
@@ -310,6 +451,10 @@ int device_factorize(const asm_desc *ds, const asm_problem *p, HostFactors &hf)
         }
     }
 done:
+    if (rc == ASM_OK && L_out) {   // keep the Cholesky factor for the backward pass
+        *L_out = dC;
+        dC = nullptr;
+    }
     if (dC) cudaFree(dC);
     if (dK) cudaFree(dK);
     if (dG) cudaFree(dG);
@@ -322,6 +467,58 @@ done:
     if (dinfo) cudaFree(dinfo);
     if (bh) cublasDestroy(bh);
     if (sh) cusolverDnDestroy(sh);
+    return rc;
+}
+
+// Cholesky factor of C on the device (column-major lower), for a problem whose
+// factors were given but whose covariance is known.
+int device_cholesky(const double *C, int M, double **L_out)
+{
+    cusolverDnHandle_t sh = nullptr;
+    double *dC = nullptr, *dwork = nullptr;
+    int *dinfo = nullptr;
+    int rc = ASM_OK, lwork = 0, info = 0;
+    CK_SOLVER(cusolverDnCreate(&sh));
+    CK_CUDA(cudaMalloc(&dC, sizeof(double) * M * M));
+    CK_CUDA(cudaMalloc(&dinfo, sizeof(int)));
+    CK_CUDA(cudaMemcpy(dC, C, sizeof(double) * M * M, cudaMemcpyHostToDevice));
+    CK_SOLVER(cusolverDnDpotrf_bufferSize(sh, CUBLAS_FILL_MODE_LOWER, M, dC, M, &lwork));
+    CK_CUDA(cudaMalloc(&dwork, sizeof(double) * std::max(lwork, 1)));
+    CK_SOLVER(cusolverDnDpotrf(sh, CUBLAS_FILL_MODE_LOWER, M, dC, M, dwork, lwork, dinfo));
+    CK_CUDA(cudaMemcpy(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost));
+    if (info != 0) rc = ASM_ERR_NOT_SPD;
+done:
+    if (rc == ASM_OK) {
+        *L_out = dC;
+        dC = nullptr;
+    }
+    if (dC) cudaFree(dC);
+    if (dwork) cudaFree(dwork);
+    if (dinfo) cudaFree(dinfo);
+    if (sh) cusolverDnDestroy(sh);
+    return rc;
+}
+
+// K~_theta_p = L^{-1} dK/dtheta_p for every parameter (same trsm as the kernel).
+int whiten_dK(asm_problem *p, const double *dK)
+{
+    const int M = p->M, N = p->N, P = p->P;
+    int rc = ASM_OK;
+    const double one = 1.0;
+    std::vector<float> h32;
+    CK_CUDA(cudaMalloc(&p->d_Kth64, sizeof(double) * (size_t)P * M * N));
+    CK_CUDA(cudaMalloc(&p->d_Kth32, sizeof(float) * (size_t)P * M * N));
+    CK_CUDA(cudaMemcpy(p->d_Kth64, dK, sizeof(double) * (size_t)P * M * N, cudaMemcpyHostToDevice));
+    for (int pi = 0; pi < P; ++pi)
+        CK_CUBLAS(cublasDtrsm(p->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T,
+                              CUBLAS_DIAG_NON_UNIT, N, M, &one, p->d_L, M, p->d_Kth64 + (size_t)pi * M * N, N));
+    {
+        std::vector<double> h((size_t)P * M * N);
+        CK_CUDA(cudaMemcpy(h.data(), p->d_Kth64, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+        h32.assign(h.begin(), h.end());
+    }
+    CK_CUDA(cudaMemcpy(p->d_Kth32, h32.data(), sizeof(float) * h32.size(), cudaMemcpyHostToDevice));
+done:
     return rc;
 }
 
@@ -500,6 +697,78 @@ int pick_kv(int max_nb, int vec, int S, int kmax)
     return kv <= kmax ? kv : -1;
 }
 
+// Snapshot of all chains into the moments of the backward pass (every
+// ASM_SNAPSHOT_EVERY kept sweeps): Sff += F^T F, Sf += column sums of F and,
+// with grid parameters, the scores s_p = r~ . (K~_theta_p f) into Sfs, Ss.
+template <class T>
+int moment_update(asm_problem *p, const WsLayout &L, int chains)
+{
+    char *ws = (char *)p->ws;
+    const int N = p->N, M = p->M;
+    const T *Fraw = (const T *)(ws + L.F);
+    double *shift = (double *)(ws + L.shift);
+    if (p->nsnap == 0) {   // centre every snapshot on the first one's mean (keeps FP32 GEMMs accurate)
+        shift_kernel<T><<<(N + 127) / 128, 128, 0, p->stream>>>(Fraw, L.ldF, chains, N, shift);
+        ++p->other_launches;
+        if (p->P > 0) {
+            kshift_kernel<<<(M * p->P + 127) / 128, 128, 0, p->stream>>>(p->d_Kth64, shift, M, N, p->P,
+                                                                        (double *)(ws + L.kshift));
+            ++p->other_launches;
+        }
+    }
+    {
+        const long long tot = (long long)chains * L.ldF;
+        center_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, p->stream>>>(Fraw, L.ldF, chains, N, shift,
+                                                                               (T *)(ws + L.D));
+        ++p->other_launches;
+    }
+    const T *F = (const T *)(ws + L.D);
+    if (cublasSetStream(p->blas, p->stream) != CUBLAS_STATUS_SUCCESS) return ASM_ERR_CUDA;
+    if constexpr (sizeof(T) == 8) {
+        const double one = 1.0;
+        if (cublasDgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_T, N, N, chains, &one, F, L.ldF, F, L.ldF, &one,
+                        (double *)(ws + L.Sff), N) != CUBLAS_STATUS_SUCCESS)
+            return ASM_ERR_CUDA;
+    } else {
+        const float one = 1.f, zero = 0.f;
+        if (cublasSgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_T, N, N, chains, &one, F, L.ldF, F, L.ldF, &zero,
+                        (float *)(ws + L.Gtmp), N) != CUBLAS_STATUS_SUCCESS)
+            return ASM_ERR_CUDA;
+        const long long nn = (long long)N * N;
+        add_f32_to_f64<<<(unsigned)((nn + 255) / 256), 256, 0, p->stream>>>((const float *)(ws + L.Gtmp),
+                                                                            (double *)(ws + L.Sff), nn);
+        ++p->other_launches;
+    }
+    colsum_kernel<T><<<(N + 127) / 128, 128, 0, p->stream>>>(F, L.ldF, chains, N, (double *)(ws + L.Sf));
+    ++p->other_launches;
+    for (int pi = 0; pi < p->P; ++pi) {
+        T *Y = (T *)(ws + L.Y);
+        cublasStatus_t st;
+        if constexpr (sizeof(T) == 8) {
+            const double one = 1.0, zero = 0.0;
+            st = cublasDgemm(p->blas, CUBLAS_OP_T, CUBLAS_OP_N, M, chains, N, &one, p->d_Kth64 + (size_t)pi * M * N,
+                             N, F, L.ldF, &zero, Y, M);
+        } else {
+            const float one = 1.f, zero = 0.f;
+            st = cublasSgemm(p->blas, CUBLAS_OP_T, CUBLAS_OP_N, M, chains, N, &one, p->d_Kth32 + (size_t)pi * M * N,
+                             N, F, L.ldF, &zero, Y, M);
+        }
+        if (st != CUBLAS_STATUS_SUCCESS) return ASM_ERR_CUDA;
+        score_kernel<T><<<(unsigned)(((long long)chains * 32 + 255) / 256), 256, 0, p->stream>>>(
+            (const T *)(ws + L.R), L.ldR, Y, (const double *)(ws + L.kshift), M, chains, p->P, pi,
+            (double *)(ws + L.Sq));
+        ++p->other_launches;
+    }
+    if (p->P > 0) {
+        fs_kernel<T><<<(N + 127) / 128, 128, 0, p->stream>>>(F, L.ldF, (const double *)(ws + L.Sq), chains, N, p->P,
+                                                             (double *)(ws + L.Sfs), (double *)(ws + L.Ss));
+        ++p->other_launches;
+    }
+    if (cudaGetLastError() != cudaSuccess) return ASM_ERR_CUDA;
+    p->nsnap += chains;
+    return ASM_OK;
+}
+
 template <class T>
 int run_sweeps(asm_problem *p, const WsLayout &L, int chains, long long s_begin, long long s_end,
                long long burn_abs)
@@ -514,7 +783,12 @@ int run_sweeps(asm_problem *p, const WsLayout &L, int chains, long long s_begin,
     char *ws = (char *)p->ws;
     long long s = s_begin;
     while (s < s_end) {
-        const long long seg = std::min<long long>(kRefreshPeriod - (s % kRefreshPeriod), s_end - s);
+        long long seg = std::min<long long>(kRefreshPeriod - (s % kRefreshPeriod), s_end - s);
+        if (p->moments) {   // also stop at the next snapshot of the kept sweeps
+            const long long k = s < burn_abs ? -1 : (s - burn_abs) / ASM_SNAPSHOT_EVERY;
+            const long long next = burn_abs + (k + 1) * ASM_SNAPSHOT_EVERY;
+            seg = std::min(seg, next - s);
+        }
         sp.sweep0 = s;
         sp.nsweeps = seg;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -531,6 +805,10 @@ int run_sweeps(asm_problem *p, const WsLayout &L, int chains, long long s_begin,
         if (p->timing && cudaEventRecord(e1, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
         ++p->sweep_launches;
         s += seg;
+        if (p->moments && s > burn_abs && (s - burn_abs) % ASM_SNAPSHOT_EVERY == 0) {
+            const int rc = moment_update<T>(p, L, chains);
+            if (rc != ASM_OK) return rc;
+        }
         if (s % kRefreshPeriod == 0) {
             refresh_kernel<T><<<chains, 128, sizeof(double) * p->N, p->stream>>>(
                 p->M, p->N, p->d_KtT, p->d_gt, sp.F, sp.ldF, sp.R, sp.ldR, (double *)(ws + L.chi2),
@@ -553,6 +831,9 @@ int init_chains(asm_problem *p, const WsLayout &L, int chains)
     if (cudaGetLastError() != cudaSuccess) return ASM_ERR_CUDA;
     if (cudaMemsetAsync(ws + L.R, 0, (size_t)chains * L.ldR * sizeof(T), p->stream) != cudaSuccess)
         return ASM_ERR_CUDA;
+    // snapshot moments of the backward pass start at zero
+    if (cudaMemsetAsync(ws + L.Sff, 0, L.Gtmp - L.Sff, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
+    p->nsnap = 0;
     refresh_kernel<T><<<chains, 128, sizeof(double) * p->N, p->stream>>>(
         p->M, p->N, p->d_KtT, p->d_gt, (const T *)(ws + L.F), L.ldF, (T *)(ws + L.R), L.ldR,
         (double *)(ws + L.chi2), (Counters *)(ws + L.counters), 0);
@@ -668,6 +949,12 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
         for (int i = 0; i < N; ++i) p->w[i] = ds->w[i];
     }
 
+    if (ds->P < 0 || (ds->P > 0 && (!ds->dK_dtheta || !ds->dw_dtheta))) { delete p; return ASM_ERR_ARG; }
+    p->P = ds->P;
+    if (p->P > 0 && (!all_finite(ds->dK_dtheta, (size_t)p->P * M * N) || !all_finite(ds->dw_dtheta, (size_t)p->P * N))) {
+        delete p;
+        return ASM_ERR_NONFINITE;
+    }
     HostFactors hf;
     int rc = ASM_OK;
     if (given) {
@@ -687,8 +974,29 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
             delete p;
             return ASM_ERR_NONFINITE;
         }
-        rc = device_factorize(ds, p, hf);
+        rc = device_factorize(ds, p, hf, &p->d_L);
         if (rc != ASM_OK) { delete p; return rc; }
+    }
+    if (given && ds->C) {
+        if (!all_finite(ds->C, (size_t)M * M)) { delete p; return ASM_ERR_NONFINITE; }
+        rc = device_cholesky(ds->C, M, &p->d_L);
+        if (rc != ASM_OK) { asm_destroy(p); return rc; }
+    }
+    if (cublasCreate(&p->blas) != CUBLAS_STATUS_SUCCESS) { asm_destroy(p); return ASM_ERR_CUDA; }
+    if (p->P > 0) {
+        if (!p->d_L) { asm_destroy(p); return ASM_ERR_ARG; }   // theta-gradients need C
+        rc = whiten_dK(p, ds->dK_dtheta);
+        if (rc != ASM_OK) { asm_destroy(p); return rc; }
+    }
+    {
+        std::vector<double> dwv(ds->P > 0 ? ds->dw_dtheta : nullptr,
+                                ds->P > 0 ? ds->dw_dtheta + (size_t)ds->P * N : nullptr);
+        if (dwv.empty()) dwv.assign(1, 0.0);
+        if ((rc = upload((void **)&p->d_w, p->w)) || (rc = upload((void **)&p->d_dw, dwv)) ||
+            cudaMalloc(&p->d_vjp, sizeof(double) * (3 * (size_t)N + M + std::max(p->P, 1))) != cudaSuccess) {
+            asm_destroy(p);
+            return rc ? rc : ASM_ERR_CUDA;
+        }
     }
     // properness: every zero mode must change sign (both bounds finite)
     for (int b = 0; b < nb; ++b) {
@@ -764,6 +1072,7 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
     p->ws_bytes = workspace_bytes;
     int rc;
     if (!cont) {
+        p->moments = (flags & ASM_SAMPLE_MOMENTS) != 0;
         p->chains = chains;
         p->precision = precision;
         p->seed = seed;
@@ -832,6 +1141,52 @@ int asm_average(asm_problem *p, double *mean_A, double *sem_A, double *ess, doub
         if (ess) ess[n] = s2 > 0.0 ? var / s2 : NAN;
     }
     return ASM_OK;
+}
+
+int asm_backward(asm_problem *p, const double *v, double *grad_G, double *grad_theta)
+{
+    if (!p || !v) return ASM_ERR_ARG;
+    if (!p->have_run || !p->moments || p->nsnap < 2) return ASM_ERR_STATE;
+    if (grad_G && !p->d_L) return ASM_ERR_STATE;
+    if (grad_theta && p->P == 0) return ASM_ERR_ARG;
+    Counters c{};
+    int rc = read_counters(p, &c);
+    if (rc != ASM_OK) return rc;
+    if (c.timeouts) return ASM_ERR_TIMEOUT;
+    const int N = p->N, M = p->M;
+    const WsLayout L = ws_layout(p, p->chains, p->precision);
+    const char *ws = (const char *)p->ws;
+    std::vector<double> hv(2 * (size_t)N);
+    for (int n = 0; n < N; ++n) {
+        hv[n] = v[n] / p->w[n];   // cotangent of fbar
+        hv[N + n] = v[n];
+    }
+    double *d_vp = p->d_vjp, *d_v = p->d_vjp + N, *d_u = p->d_vjp + 2 * N, *d_y = p->d_vjp + 3 * N,
+           *d_g = p->d_vjp + 3 * N + M;
+    const double ns = (double)p->nsnap;
+    if (cudaMemcpyAsync(d_vp, hv.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    if (grad_G) {
+        vjp_cov_kernel<<<(N + 127) / 128, 128, 0, p->stream>>>((const double *)(ws + L.Sff),
+                                                               (const double *)(ws + L.Sf), ns, d_vp, N, d_u);
+        const double one = 1.0, zero = 0.0;
+        if (cudaGetLastError() != cudaSuccess || cublasSetStream(p->blas, p->stream) != CUBLAS_STATUS_SUCCESS ||
+            cublasDgemv(p->blas, CUBLAS_OP_N, M, N, &one, p->d_KtT, M, d_u, 1, &zero, d_y, 1) !=
+                CUBLAS_STATUS_SUCCESS ||
+            cublasDtrsv(p->blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, M, p->d_L, M, d_y, 1) !=
+                CUBLAS_STATUS_SUCCESS ||
+            cudaMemcpyAsync(grad_G, d_y, sizeof(double) * M, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+            return ASM_ERR_CUDA;
+    }
+    if (grad_theta) {
+        vjp_theta_kernel<<<(p->P + 31) / 32, 32, 0, p->stream>>>(
+            (const double *)(ws + L.Sfs), (const double *)(ws + L.Ss), (const double *)(ws + L.Sf),
+            (const double *)(ws + L.shift), ns, d_vp, d_v, p->d_w, p->d_dw, N, p->P, d_g);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(grad_theta, d_g, sizeof(double) * p->P, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+            return ASM_ERR_CUDA;
+    }
+    return cudaStreamSynchronize(p->stream) == cudaSuccess ? ASM_OK : ASM_ERR_CUDA;
 }
 
 int asm_chain_state(asm_problem *p, double *f, double *chi2)
@@ -917,6 +1272,7 @@ int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, ui
     p->timing = false;
     p->ws = scratch;
     p->ws_bytes = ASM_NOALLOC_SCRATCH_BYTES;
+    p->moments = false;
     p->chains = chains;
     p->precision = precision;
     p->seed = seed;
@@ -1021,7 +1377,9 @@ int asm_restore(asm_problem *p, const void *host_buf, size_t bytes, void *d_work
 void asm_destroy(asm_problem *p)
 {
     if (!p) return;
-    void *ptrs[] = {p->d_level_first, p->d_level_nblocks, p->d_blocks, p->d_KtT, p->d_gt};
+    void *ptrs[] = {p->d_level_first, p->d_level_nblocks, p->d_blocks, p->d_KtT, p->d_gt, p->d_L,
+                    p->d_Kth64, p->d_Kth32, p->d_w, p->d_dw, p->d_vjp};
+    if (p->blas) cublasDestroy(p->blas);
     for (void *x : ptrs)
         if (x) cudaFree(x);
     free_prec(p->b64);

@@ -287,3 +287,93 @@ def levels_flat(levels) -> tuple[np.ndarray, np.ndarray]:
     nb = np.array([len(l) for l in levels], dtype=np.int32)
     bs = np.concatenate([np.asarray(l, dtype=np.int32) for l in levels]).astype(np.int32)
     return nb, bs
+
+
+# --------------------------------------------------------------------------
+# grid-density (default-model) parameters theta for the differentiation
+# workload: a mixture of three Gaussians truncated to [a, b]
+#   theta = (c1, c2, c3, log s1, log s2, log s3, a2, a3), weights softmax(0, a2, a3)
+# grid x_n = P^{-1}((n - 1/2)/N), weights w_n = 1/(N rho(x_n)) (Sec. V.B).
+# --------------------------------------------------------------------------
+
+THETA0 = np.array([-3.0, 0.0, 3.0, np.log(2.0), np.log(2.0), np.log(2.0), 0.0, 0.0])
+
+
+def _mixture(theta):
+    c = np.asarray(theta[:3], dtype=np.float64)
+    s = np.exp(np.asarray(theta[3:6], dtype=np.float64))
+    a = np.array([0.0, theta[6], theta[7]])
+    pi = np.exp(a - a.max())
+    return c, s, pi / pi.sum()
+
+
+def mixture_cdf_pdf(x, theta, a=-6.0, b=6.0):
+    """CDF and density of the truncated mixture at x."""
+    c, s, pi = _mixture(theta)
+    x = np.asarray(x, dtype=np.float64)[..., None]
+    Z = np.sum(pi * (special.ndtr((b - c) / s) - special.ndtr((a - c) / s)))
+    cdf = np.sum(pi * (special.ndtr((x - c) / s) - special.ndtr((a - c) / s)), axis=-1) / Z
+    pdf = np.sum(pi * np.exp(-0.5 * ((x - c) / s) ** 2) / (s * math.sqrt(2 * math.pi)), axis=-1) / Z
+    return cdf, pdf
+
+
+def mixture_grid(theta, N, a=-6.0, b=6.0):
+    """x_n = P^{-1}((n - 1/2)/N) by bisection then Newton, and w_n = 1/(N rho(x_n))."""
+    z = (np.arange(N) + 0.5) / N
+    lo, hi = np.full(N, a), np.full(N, b)
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        cm, _ = mixture_cdf_pdf(mid, theta, a, b)
+        lo, hi = np.where(cm < z, mid, lo), np.where(cm < z, hi, mid)
+    x = 0.5 * (lo + hi)
+    for _ in range(3):
+        cm, pm = mixture_cdf_pdf(x, theta, a, b)
+        x = x - (cm - z) / pm
+    _, pm = mixture_cdf_pdf(x, theta, a, b)
+    return x, 1.0 / (N * pm)
+
+
+def fermionic_kernel_domega(tau, omega, beta):
+    """dK/d omega of the fermionic kernel: K (-tau + beta / (1 + e^{beta omega}))."""
+    K = fermionic_kernel(tau, omega, beta)
+    t = np.asarray(tau, dtype=np.float64)[:, None]
+    w = np.asarray(omega, dtype=np.float64)[None, :]
+    return K * (-t + beta * special.expit(-beta * w))
+
+
+def theta_problem(theta=None, N=200, M=64, beta=16.0, noise=1e-4, seed=1004, offset=0.0,
+                  levels=None, h=1e-6):
+    """The differentiation workload on the theta-grid: K(theta) acting on fbar,
+    w(theta), dK/dtheta (P x M x N), dw/dtheta (P x N).  The data G are made
+    once from the true spectrum on a fine grid, so they do not depend on theta."""
+    theta = THETA0.copy() if theta is None else np.asarray(theta, dtype=np.float64)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cs = rng.uniform(-4.0, 4.0, 3)
+    ss = rng.uniform(0.2, 1.0, 3)
+    ws = rng.dirichlet(np.ones(3))
+    A = lambda om: sum(ws[i] * gauss_pdf(om, cs[i], ss[i]) for i in range(3)) + offset
+    tau = tau_grid(beta, M)
+    fine, dfine = uniform_grid(-6.0, 6.0, 24000)
+    G0 = fermionic_kernel(tau, fine, beta) @ (A(fine) * dfine)
+    C = np.eye(M) * noise * noise
+    G = G0 + np.linalg.cholesky(C) @ rng.standard_normal(M)
+    x, w = mixture_grid(theta, N)
+    K = fermionic_kernel(tau, x, beta)
+    P = len(theta)
+    dx = np.zeros((P, N))
+    dw = np.zeros((P, N))
+    for p_ in range(P):
+        e = np.zeros(P)
+        e[p_] = h
+        xp, wp = mixture_grid(theta + e, N)
+        xm, wm = mixture_grid(theta - e, N)
+        dx[p_] = (xp - xm) / (2 * h)
+        dw[p_] = (wp - wm) / (2 * h)
+    dK = fermionic_kernel_domega(tau, x, beta)[None, :, :] * dx[:, None, :]
+    if levels is None:
+        levels = [[0], equal_blocks(N, 8)] if N >= 16 else [[0]]
+    prob = Problem(f"theta_grid_N{N}_M{M}", K, G, C, x, w, [np.asarray(l, np.int32) for l in levels],
+                   A(x) * w, chains=4096, burn_in=500, sweeps=5000)
+    prob.extra.update({"theta": theta, "dK_dtheta": dK, "dw_dtheta": dw, "dx_dtheta": dx, "beta": beta,
+                       "tau": tau})
+    return prob
