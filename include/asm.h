@@ -109,6 +109,11 @@ typedef struct {
     int64_t timed_launches;     /* sweep launches timed with ASM_SAMPLE_TIMING */
     double sweep_kernel_ms;     /* summed event-timed duration of those launches */
     int64_t timeouts;           /* bounded device waits that gave up (0 in a valid run) */
+    int64_t graph_replays;      /* refresh periods run as replays of the handle's CUDA graph */
+    int32_t team_lanes;         /* lanes per chain of the last sweep launch */
+    int32_t consumers_per_cta;  /* chain warps per CTA of the last sweep launch */
+    int32_t ctas;               /* CTAs of the last sweep launch (persistent) */
+    int32_t work_items;         /* (problem, chain group) items of the last sweep launch */
 } asm_stats;
 
 /* Set-up (Sec. IV: whitening C^{-1} = T^T T by Cholesky, K~ = T K, g~ = T G;
@@ -118,8 +123,36 @@ typedef struct {
  * mode.  On success *out receives a new handle (free with asm_destroy). */
 int asm_setup(const asm_desc *d, asm_problem **out);
 
-/* Bytes of device workspace asm_sample needs for `chains` chains at
- * `precision` (ASM_FP64 or ASM_MIXED); 0 for invalid arguments. */
+/* Set-up of n independent problems as one batch handle (each problem as in
+ * asm_setup; n >= 1, d points to n descriptors).  asm_sample on it runs every
+ * problem's chains in the same persistent launches (work items = (problem,
+ * chain group), costliest problems first); problem k keys its random numbers
+ * with problem id P + k, P the handle's problem id (asm_set_stream_ids,
+ * default 0), so problem k of a batch gives exactly what a single handle of
+ * that problem gives with problem id P + k.  Results per problem:
+ * asm_average_at.  Backward moments, chain states and checkpoints are for
+ * single problems (ASM_ERR_ARG on a batch).  On failure nothing is kept. */
+int asm_setup_batch(int n, const asm_desc *d, asm_problem **out);
+
+/* Number of problems of a handle (1 for asm_setup). */
+int asm_problem_count(const asm_problem *p);
+
+/* Autotuner of the sweep launch (no counterpart in the paper).  Times every
+ * candidate shape -- lanes per chain S in {32, 16, 8} times chain warps per
+ * CTA in {heuristic, 2, 4, 6, 7, 8}, where it fits -- on one warm-up and three
+ * timed sweeps of fresh trial chains in the caller's workspace (same layout
+ * and size rule as asm_sample), and keeps the fastest for later asm_sample
+ * calls on p.  The shape changes no result: every chain does the same
+ * arithmetic in the same order under every shape.  The workspace's contents
+ * are overwritten, so the next asm_sample must start fresh chains
+ * (ASM_SAMPLE_CONTINUE then fails with ASM_ERR_STATE).  Synchronises
+ * `stream`.  team_out / consumers_out (may be NULL) receive the choice
+ * (consumers 0 = the built-in heuristic). */
+int asm_tune(asm_problem *p, int chains, int precision, void *d_workspace, size_t workspace_bytes,
+             void *stream, int *team_out, int *consumers_out);
+
+/* Bytes of device workspace asm_sample needs for `chains` chains (per problem)
+ * at `precision` (ASM_FP64 or ASM_MIXED); 0 for invalid arguments. */
 size_t asm_workspace_bytes(const asm_problem *p, int chains, int precision);
 
 /* Run burn_in + sweeps sweeps of `chains` independent chains (Sec. IV.C: every
@@ -137,6 +170,13 @@ size_t asm_workspace_bytes(const asm_problem *p, int chains, int precision);
  * otherwise chains start from the flat default-model scale fit.
  * ASM_SAMPLE_TIMING records a CUDA event pair on `stream` around every sweep
  * launch; asm_status reports their summed duration.
+ * Launches: one persistent sweep kernel per refresh period (64 sweeps) over
+ * every (problem, chain group) work item, then the FP64 residual refresh.
+ * Runs of whole periods replay a CUDA graph of (advance the sweep range,
+ * sweep, refresh), instantiated on the first such call and kept in the handle
+ * until the workspace, chain count, precision or launch shape changes; not
+ * with ASM_SAMPLE_TIMING, ASM_SAMPLE_MOMENTS, or while `stream` is being
+ * captured (then each launch is issued directly). 
  * d_workspace: device pointer, 256-byte aligned, >= asm_workspace_bytes(). */
 int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t seed,
                int precision, uint32_t flags, void *d_workspace, size_t workspace_bytes,
@@ -162,6 +202,9 @@ int asm_average(asm_problem *p, double *mean_A, double *sem_A, double *ess, doub
  * grad_G needs the covariance C (computed or given at set-up); grad_theta needs
  * P > 0; either pointer may be NULL. */
 int asm_backward(asm_problem *p, const double *v, double *grad_G, double *grad_theta);
+
+/* asm_average for problem k of a handle (k = 0 for a single problem). */
+int asm_average_at(asm_problem *p, int k, double *mean_A, double *sem_A, double *ess, double *mean_fbar);
 
 /* Current chain states (synchronises): f (chains x N, FP64 copy of fbar) and
  * chi2 (chains) = |r~|^2 of the residual the sampler tracks; either may be NULL. */

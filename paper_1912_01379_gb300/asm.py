@@ -41,12 +41,14 @@ class asm_stats(ct.Structure):
                 ("nonfinite_moves", ct.c_int64), ("max_resync_drift", ct.c_double),
                 ("sweep_launches", ct.c_int64), ("other_launches", ct.c_int64),
                 ("timed_launches", ct.c_int64), ("sweep_kernel_ms", ct.c_double),
-                ("timeouts", ct.c_int64)]
+                ("timeouts", ct.c_int64), ("graph_replays", ct.c_int64), ("team_lanes", ct.c_int32),
+                ("consumers_per_cta", ct.c_int32), ("ctas", ct.c_int32), ("work_items", ct.c_int32)]
 
 
 EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",
            "asm_status", "asm_destroy", "asm_error_string", "asm_sample_noalloc", "asm_set_stream_ids",
-           "asm_checkpoint", "asm_restore", "asm_backward"]
+           "asm_checkpoint", "asm_restore", "asm_backward", "asm_setup_batch", "asm_problem_count",
+           "asm_average_at", "asm_tune"]
 ASM_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
@@ -95,6 +97,15 @@ def load(build_if_missing: bool = True):
     L.asm_restore.restype = ct.c_int
     L.asm_backward.argtypes = [ct.c_void_p, _dp, _dp, _dp]
     L.asm_backward.restype = ct.c_int
+    L.asm_setup_batch.argtypes = [ct.c_int, ct.POINTER(asm_desc), ct.POINTER(ct.c_void_p)]
+    L.asm_setup_batch.restype = ct.c_int
+    L.asm_problem_count.argtypes = [ct.c_void_p]
+    L.asm_problem_count.restype = ct.c_int
+    L.asm_average_at.argtypes = [ct.c_void_p, ct.c_int, _dp, _dp, _dp, _dp]
+    L.asm_average_at.restype = ct.c_int
+    L.asm_tune.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_size_t, ct.c_void_p,
+                           ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
+    L.asm_tune.restype = ct.c_int
     _lib = L
     return L
 
@@ -121,49 +132,43 @@ def _require_cuda():
     return torch
 
 
-class Problem:
-    """A set-up problem: owns the library handle and a torch workspace.
+def _make_desc(K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None):
+    """asm_desc of one problem plus the arrays it points into (kept alive by
+    the caller until asm_setup returns)."""
+    keep = []
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    M, N = K.shape
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    w = np.ones(N) if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    levels = [np.asarray(l, dtype=np.int32) for l in levels]
+    nb = np.array([len(l) for l in levels], dtype=np.int32)
+    bs = np.concatenate(levels).astype(np.int32)
+    d = asm_desc()
+    d.M, d.N = M, N
+    d.K, d.G, d.C, d.w = _dptr(K), _dptr(G), _dptr(C), _dptr(w)
+    d.n_levels = len(levels)
+    d.level_nblocks = nb.ctypes.data_as(_ip)
+    d.block_start = bs.ctypes.data_as(_ip)
+    keep += [K, G, C, w, nb, bs]
+    if factors is not None:
+        arrs = [np.ascontiguousarray(getattr(factors, k), dtype=np.float64) for k in ("Kt", "gt", "d", "V", "U")]
+        keep += arrs
+        d.Kt, d.gt, d.d, d.V, d.U = (_dptr(a) for a in arrs)
+    P = 0
+    if dK_dtheta is not None:
+        dK = np.ascontiguousarray(dK_dtheta, dtype=np.float64)
+        dw = np.ascontiguousarray(dw_dtheta, dtype=np.float64)
+        P = dK.shape[0]
+        assert dK.shape == (P, M, N) and dw.shape == (P, N)
+        keep += [dK, dw]
+        d.P, d.dK_dtheta, d.dw_dtheta = P, _dptr(dK), _dptr(dw)
+    return d, keep, (M, N, w, levels, P)
 
-    K (M x N, acting on fbar), G (M), C (M x M) and the levels (list of arrays
-    of block starts) follow Sec. II and IV of the paper; w are the Riemann
-    weights (A = fbar / w).  `factors` (optional) is an object with Kt, gt, d,
-    V, U arrays in the layout of asm_desc to use given singular vectors."""
 
-    def __init__(self, K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None):
-        L = load()
-        self._keep = []
-        K = np.ascontiguousarray(K, dtype=np.float64)
-        self.M, self.N = K.shape
-        G = np.ascontiguousarray(G, dtype=np.float64)
-        C = np.ascontiguousarray(C, dtype=np.float64)
-        self.w = np.ones(self.N) if w is None else np.ascontiguousarray(w, dtype=np.float64)
-        self.levels = [np.asarray(l, dtype=np.int32) for l in levels]
-        nb = np.array([len(l) for l in self.levels], dtype=np.int32)
-        bs = np.concatenate(self.levels).astype(np.int32)
-        d = asm_desc()
-        d.M, d.N = self.M, self.N
-        d.K, d.G, d.C, d.w = _dptr(K), _dptr(G), _dptr(C), _dptr(self.w)
-        d.n_levels = len(self.levels)
-        d.level_nblocks = nb.ctypes.data_as(_ip)
-        d.block_start = bs.ctypes.data_as(_ip)
-        self._keep += [K, G, C, nb, bs]
-        if factors is not None:
-            arrs = [np.ascontiguousarray(getattr(factors, k), dtype=np.float64) for k in ("Kt", "gt", "d", "V", "U")]
-            self._keep += arrs
-            d.Kt, d.gt, d.d, d.V, d.U = (_dptr(a) for a in arrs)
-        self.P = 0
-        if dK_dtheta is not None:
-            dK = np.ascontiguousarray(dK_dtheta, dtype=np.float64)
-            dw = np.ascontiguousarray(dw_dtheta, dtype=np.float64)
-            self.P = dK.shape[0]
-            assert dK.shape == (self.P, self.M, self.N) and dw.shape == (self.P, self.N)
-            self._keep += [dK, dw]
-            d.P, d.dK_dtheta, d.dw_dtheta = self.P, _dptr(dK), _dptr(dw)
-        h = ct.c_void_p()
-        _check(L.asm_setup(ct.byref(d), ct.byref(h)), "asm_setup")
-        self._h = h
-        self._ws = None
-        self.chains = 0
+class _Handle:
+    """Workspace, sampling, tuning and counters shared by single problems and
+    batches."""
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -173,10 +178,7 @@ class Problem:
     def workspace_bytes(self, chains, precision=ASM_MIXED):
         return int(load().asm_workspace_bytes(self._h, chains, precision))
 
-    def sample(self, chains, burn_in, sweeps, seed, precision=ASM_MIXED, cont=False, stream=None,
-               workspace=None, timing=False, moments=False):
-        """asm_sample on a torch workspace (allocated here unless given) and the
-        current torch stream (or `stream`)."""
+    def _workspace(self, chains, precision, workspace=None):
         torch = _require_cuda()
         need = self.workspace_bytes(chains, precision)
         if need == 0:
@@ -187,6 +189,13 @@ class Problem:
             workspace = self._ws
         else:
             self._ws = workspace
+        return torch, workspace
+
+    def sample(self, chains, burn_in, sweeps, seed, precision=ASM_MIXED, cont=False, stream=None,
+               workspace=None, timing=False, moments=False):
+        """asm_sample on a torch workspace (allocated here unless given) and the
+        current torch stream (or `stream`)."""
+        torch, workspace = self._workspace(chains, precision, workspace)
         s = stream if stream is not None else torch.cuda.current_stream()
         flags = ((ASM_SAMPLE_CONTINUE if cont else 0) | (ASM_SAMPLE_TIMING if timing else 0) |
                  (ASM_SAMPLE_MOMENTS if moments else 0))
@@ -194,6 +203,80 @@ class Problem:
                                  ct.c_void_p(workspace.data_ptr()), workspace.numel(),
                                  ct.c_void_p(s.cuda_stream)), "asm_sample")
         self.chains = chains
+
+    def tune(self, chains, precision=ASM_MIXED, stream=None, workspace=None):
+        """asm_tune: picks the fastest launch shape (lanes per chain, chain warps
+        per CTA) for `chains` chains; returns (team_lanes, consumers)."""
+        torch, workspace = self._workspace(chains, precision, workspace)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        team, cons = ct.c_int(0), ct.c_int(0)
+        _check(load().asm_tune(self._h, chains, precision, ct.c_void_p(workspace.data_ptr()), workspace.numel(),
+                               ct.c_void_p(s.cuda_stream), ct.byref(team), ct.byref(cons)), "asm_tune")
+        return team.value, cons.value
+
+    def set_stream_ids(self, problem_id=0, chain_offset=0):
+        _check(load().asm_set_stream_ids(self._h, ct.c_uint64(problem_id), ct.c_uint64(chain_offset)),
+               "asm_set_stream_ids")
+
+    def status(self):
+        st = asm_stats()
+        _check(load().asm_status(self._h, ct.byref(st)), "asm_status")
+        return {k: getattr(st, k) for k, _ in asm_stats._fields_}
+
+
+def _average(h, k, N, w):
+    mean_A, sem_A, ess, mean_f = (np.zeros(N) for _ in range(4))
+    _check(load().asm_average_at(h, k, _dptr(mean_A), _dptr(sem_A), _dptr(ess), _dptr(mean_f)),
+           "asm_average_at")
+    return {"mean_A": mean_A, "sem_A": sem_A, "ess": ess, "mean_fbar": mean_f, "sem_fbar": sem_A * w}
+
+
+class Batch(_Handle):
+    """Independent problems sampled together (asm_setup_batch): every problem's
+    chains run in the same persistent launches.  `problems` is a sequence of
+    dicts with the keyword arguments of Problem (K, G, C, levels, w, factors)."""
+
+    def __init__(self, problems):
+        L = load()
+        descs, keeps, self.shapes = [], [], []
+        for pr in problems:
+            d, keep, (M, N, w, levels, _) = _make_desc(**pr)
+            descs.append(d)
+            keeps.append(keep)
+            self.shapes.append((M, N, w))
+        arr = (asm_desc * len(descs))(*descs)
+        h = ct.c_void_p()
+        _check(L.asm_setup_batch(len(descs), arr, ct.byref(h)), "asm_setup_batch")
+        self._h = h
+        self._ws = None
+        self.chains = 0
+        assert L.asm_problem_count(h) == len(descs)
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def average(self, k):
+        M, N, w = self.shapes[k]
+        return _average(self._h, k, N, w)
+
+
+class Problem(_Handle):
+    """A set-up problem: owns the library handle and a torch workspace.
+
+    K (M x N, acting on fbar), G (M), C (M x M) and the levels (list of arrays
+    of block starts) follow Sec. II and IV of the paper; w are the Riemann
+    weights (A = fbar / w).  `factors` (optional) is an object with Kt, gt, d,
+    V, U arrays in the layout of asm_desc to use given singular vectors."""
+
+    def __init__(self, K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None):
+        L = load()
+        d, self._keep, (self.M, self.N, self.w, self.levels, self.P) = _make_desc(
+            K, G, C, levels, w, factors, dK_dtheta, dw_dtheta)
+        h = ct.c_void_p()
+        _check(L.asm_setup(ct.byref(d), ct.byref(h)), "asm_setup")
+        self._h = h
+        self._ws = None
+        self.chains = 0
 
     def sample_noalloc(self, chains, burn_in, sweeps, seed, precision, out_mean, out_sem2, out_m2,
                        stream=None):
@@ -211,12 +294,7 @@ class Problem:
         self.chains = chains
 
     def average(self):
-        N = self.N
-        mean_A, sem_A, ess, mean_f = (np.zeros(N) for _ in range(4))
-        _check(load().asm_average(self._h, _dptr(mean_A), _dptr(sem_A), _dptr(ess), _dptr(mean_f)),
-               "asm_average")
-        return {"mean_A": mean_A, "sem_A": sem_A, "ess": ess, "mean_fbar": mean_f,
-                "sem_fbar": sem_A * self.w}
+        return _average(self._h, 0, self.N, self.w)
 
     def backward(self, v, want_G=True, want_theta=None):
         """asm_backward: vector-Jacobian products of <A> for the cotangent v (N)."""
@@ -232,10 +310,6 @@ class Problem:
         chi2 = np.zeros(self.chains)
         _check(load().asm_chain_state(self._h, _dptr(f), _dptr(chi2)), "asm_chain_state")
         return f, chi2
-
-    def set_stream_ids(self, problem_id=0, chain_offset=0):
-        _check(load().asm_set_stream_ids(self._h, ct.c_uint64(problem_id), ct.c_uint64(chain_offset)),
-               "asm_set_stream_ids")
 
     def checkpoint(self) -> bytes:
         n = ct.c_size_t(0)
@@ -254,8 +328,3 @@ class Problem:
         _check(load().asm_restore(self._h, buf, len(blob), ct.c_void_p(self._ws.data_ptr()), self._ws.numel(),
                                   ct.c_void_p(s.cuda_stream)), "asm_restore")
         self.chains = chains
-
-    def status(self):
-        st = asm_stats()
-        _check(load().asm_status(self._h, ct.byref(st)), "asm_status")
-        return {k: getattr(st, k) for k, _ in asm_stats._fields_}

@@ -49,7 +49,7 @@ struct Counters {            // device counters, first bytes of the workspace
 
 template <class T>
 struct SweepParams {
-    int M, N, S;                      // S: lanes per chain (power of two, <= 32)
+    int M, N;
     int n_levels;
     const int *level_first;           // first block index of each level
     const int *level_nblocks;
@@ -59,25 +59,59 @@ struct SweepParams {
     T *R; int ldR;                    // tracked residuals, chains x ldR
     double *S1, *S2;                  // sums of f and f^2, chains x N
     int chains;
-    long long sweep0, nsweeps, burn_in;
     unsigned long long seed, problem_id;
     unsigned long long chain_offset;  // global id of local chain 0 (Philox key word)
     Counters *counters;
-    int cpad;                         // shared-memory stride of the c/w buffers (>= max np)
-    int mpad;                         // shared-memory stride of the residual (>= M)
-    // move-record pipeline, shared by the CTA: `depth` stages filled by one
-    // producer warp with bulk copies (TMA engine); `full` barriers signal a
-    // landed record, `empty` barriers collect the consumer warps' releases
-    int depth;                        // stages in the ring
+    // residual refresh / initial state of this problem (FP64)
+    const double *KtT, *gt;           // whitened kernel (N x M) and data
+    double *chi2;                     // chains
+    double f0;                        // starting value of every fbar_n
+};
+
+// What every problem of one launch shares: the CTA shape and the
+// shared-memory plan (the union of the problems' needs).  The move records
+// of a CTA's item flow through a ring of `depth` stages filled by one
+// producer warp with bulk copies (TMA engine); `full` barriers signal a
+// landed record, `empty` barriers collect the consumer warps' releases.
+struct LaunchShape {
+    int S;                            // lanes per chain (power of two, <= 32)
     int consumers;                    // consumer warps per CTA (the producer is one more)
+    int depth;                        // stages in the ring
     int off_full, off_empty, off_stages;  // byte offsets in dynamic shared memory
     int stage_bytes;                  // bytes per stage (>= the largest record)
+    int cpad;                         // shared-memory stride of the c/w buffers (>= max np)
+    int mpad;                         // shared-memory stride of the residual (>= max M)
+    int n_items;                      // (problem, chain group) work items
+};
+
+// Per-launch control block in device memory: the work queue and the launch's
+// sweep range.  Kept on the device so that one refresh period (advance the
+// range, sweep, refresh) is a fixed sequence that a CUDA graph can replay.
+struct RunCtrl {
+    int queue;                        // next work item
+    int pad_;
+    long long sweep0, nsweeps;        // sweeps [sweep0, sweep0 + nsweeps)
+    long long burn_in;                // absolute sweep index where accumulation starts
+};
+
+// A work item: problem index and chain group (consumers x 32/S chains).
+struct WorkItem {
+    int problem, group;
 };
 
 // Launchers (asm_sweep_f32.cu / asm_sweep_f64.cu).  kv: 16-byte vectors per lane.
-// The CTA has p.consumers consumer warps and one producer warp.
-cudaError_t launch_sweeps_f32(const SweepParams<float> &p, int kv, cudaStream_t s);
-cudaError_t launch_sweeps_f64(const SweepParams<double> &p, int kv, cudaStream_t s);
+// Persistent: `ctas` CTAs of (consumers + 1) warps pull work items from
+// ctrl->queue (reset to 0 before the launch).  One problem (batch = false):
+// its parameters p0 travel by value in the launch; several (batch = true):
+// work item problems index the device array probs.
+cudaError_t launch_sweeps_f32(const SweepParams<float> &p0, const SweepParams<float> *probs, const WorkItem *items,
+                              RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch, int ctas, cudaStream_t s);
+cudaError_t launch_sweeps_f64(const SweepParams<double> &p0, const SweepParams<double> *probs,
+                              const WorkItem *items, RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch,
+                              int ctas, cudaStream_t s);
+// CTAs of the persistent kernel that fit one SM at this shape (shared memory included).
+int sweep_ctas_per_sm_f32(const LaunchShape &shape, int kv, bool batch);
+int sweep_ctas_per_sm_f64(const LaunchShape &shape, int kv, bool batch);
 // Largest supported kv per precision.
 constexpr int kMaxKvF32 = 16;   // 64 floats per lane
 constexpr int kMaxKvF64 = 32;   // 64 doubles per lane

@@ -80,6 +80,61 @@ __global__ void refresh_kernel(int M, int N, const double *__restrict__ KtT, con
     }
 }
 
+// The same refresh for every chain of every problem of a launch: CTA b handles
+// chain b % chains of problem b / chains (parameters from the launch's table).
+template <class T>
+__global__ void refresh_all_kernel(const SweepParams<T> *__restrict__ probs, int chains, int track_drift)
+{
+    extern __shared__ double fs[];
+    __shared__ double red_old[32], red_new[32];
+    const SweepParams<T> &p = probs[blockIdx.x / chains];
+    const int q = blockIdx.x % chains;
+    const int M = p.M, N = p.N;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) fs[n] = (double)p.F[(size_t)q * p.ldF + n];
+    __syncthreads();
+    double so = 0.0, sn = 0.0;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        double a = p.gt[m];
+        for (int n = 0; n < N; ++n) a -= p.KtT[(size_t)n * M + m] * fs[n];
+        const double old = (double)p.R[(size_t)q * p.ldR + m];
+        so += old * old;
+        sn += a * a;
+        p.R[(size_t)q * p.ldR + m] = (T)a;
+    }
+    for (int off = 16; off; off >>= 1) {
+        so += __shfl_xor_sync(0xffffffffu, so, off);
+        sn += __shfl_xor_sync(0xffffffffu, sn, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red_old[threadIdx.x >> 5] = so;
+        red_new[threadIdx.x >> 5] = sn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red_old[w]; b += red_new[w]; }
+        p.chi2[q] = b;
+        if (track_drift) {
+            const double drift = fabs(a - b) / fmax(b, 1e-300);
+            atomicMax(&p.counters->drift_bits, (unsigned long long)__double_as_longlong(drift));
+        }
+    }
+}
+
+// Sets the launch's sweep range (advance = 0) or moves it on by its length
+// (advance = 1), and resets the work queue.
+__global__ void ctrl_kernel(RunCtrl *c, long long sweep0, long long nsweeps, long long burn_in, int advance)
+{
+    c->queue = 0;
+    if (advance) {
+        c->sweep0 += c->nsweeps;
+    } else {
+        c->sweep0 = sweep0;
+        c->nsweeps = nsweeps;
+        c->burn_in = burn_in;
+    }
+}
+
 // Per grid point: mean over chains and kept sweeps, the spread of the chain
 // means (two passes) and the second moment.
 __global__ void reduce_kernel(const double *S1, const double *S2, int chains, int N, double kept,
@@ -266,8 +321,11 @@ struct asm_problem {
     bool moments = false;
     long long nsnap = 0;                   // chain snapshots in the moments
     PrecBuffers b64, b32;
+    // batch: one sub-handle per problem (empty for a single problem)
+    std::vector<asm_problem *> kids;
     // run state
-    void *ws = nullptr;
+    void *ws_all = nullptr;   // the caller's workspace (header + every problem's section)
+    void *ws = nullptr;       // this problem's section of it
     size_t ws_bytes = 0;
     int chains = 0, precision = -1, team = 32;
     long long sweeps_done = 0, kept = 0;
@@ -276,6 +334,27 @@ struct asm_problem {
     unsigned long long next_problem_id = 0, next_chain_offset = 0;
     cudaStream_t stream = nullptr;
     bool have_run = false;
+    // launch shape chosen by asm_tune (0: the built-in heuristic)
+    int tuned_consumers = 0;
+    // one refresh period (advance the range, sweep, refresh) as a CUDA graph
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    struct GraphKey {
+        const void *ws_all = nullptr;
+        int chains = 0, precision = -1, kv = 0, ctas = 0, S = 0, consumers = 0, depth = 0, n_items = 0;
+        size_t refresh_smem = 0;
+        unsigned long long seed = 0, problem_id = 0, chain_offset = 0;
+        bool operator==(const GraphKey &o) const
+        {
+            return ws_all == o.ws_all && chains == o.chains && precision == o.precision && kv == o.kv &&
+                   ctas == o.ctas && S == o.S && consumers == o.consumers && depth == o.depth &&
+                   n_items == o.n_items && refresh_smem == o.refresh_smem && seed == o.seed &&
+                   problem_id == o.problem_id && chain_offset == o.chain_offset;
+        }
+    } gkey;
+    long long graph_replays = 0;
+    int last_team = 0, last_consumers = 0, last_ctas = 0, last_items = 0;   // shape of the last sweep launch
+    bool no_graph = false;    // direct launches only (the allocation-free entry point)
     // launch bookkeeping
     long long sweep_launches = 0, other_launches = 0, timed_launches = 0;
     double timed_ms = 0.0;
@@ -312,6 +391,44 @@ WsLayout ws_layout(const asm_problem *p, int chains, int precision)
     L.D = off; off = align_up(off + (size_t)chains * L.ldF * es, 256);
     L.total = off;
     return L;
+}
+
+// The problems a handle samples: itself, or every problem of a batch.
+std::vector<asm_problem *> units_of(asm_problem *p)
+{
+    if (p->kids.empty()) return {p};
+    return p->kids;
+}
+std::vector<const asm_problem *> units_of(const asm_problem *p)
+{
+    if (p->kids.empty()) return {p};
+    return std::vector<const asm_problem *>(p->kids.begin(), p->kids.end());
+}
+
+// Workspace = header (launch control, work items, per-problem launch parameters)
+// followed by one section per problem.
+struct RunLayout {
+    size_t ctrl, items, probs, header;
+    std::vector<size_t> unit;   // offset of each problem's section
+    size_t total;
+};
+
+RunLayout run_layout(const asm_problem *p, int chains, int precision)
+{
+    RunLayout R{};
+    const auto us = units_of(p);
+    const size_t nu = us.size();
+    R.ctrl = 0;
+    R.items = 256;
+    R.probs = align_up(R.items + nu * (size_t)chains * sizeof(WorkItem), 256);
+    R.header = align_up(R.probs + nu * sizeof(SweepParams<double>), 256);
+    size_t off = R.header;
+    for (const asm_problem *u : us) {
+        R.unit.push_back(off);
+        off = align_up(off + ws_layout(u, chains, precision).total, 256);
+    }
+    R.total = off;
+    return R;
 }
 
 template <class T>
@@ -620,7 +737,6 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     SweepParams<T> sp{};
     sp.M = p->M;
     sp.N = p->N;
-    sp.S = p->team;
     sp.n_levels = p->n_levels;
     sp.level_first = p->d_level_first;
     sp.level_nblocks = p->d_level_nblocks;
@@ -644,49 +760,75 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.problem_id = p->problem_id;
     sp.chain_offset = p->chain_offset;
     sp.counters = (Counters *)(ws + L.counters);
-    sp.cpad = round_up_int(std::max(p->max_np, 1), 32);
-    sp.mpad = round_up_int(p->M, 32);
     sp.pd.meta = (const T *)b.meta;
     sp.pd.rec = (const T *)b.rec;
+    sp.KtT = p->d_KtT;
+    sp.gt = p->d_gt;
+    sp.chi2 = (double *)(ws + L.chi2);
+    sp.f0 = p->f0;
     return sp;
 }
 
 // Shared memory of the sweep kernel: per team c, w and r~; the ring's `full`
-// and `empty` barriers and `depth` record stages.  Consumer warps per CTA are
-// chosen so that the CTAs about cover the SMs once (all chains of an SM then
-// share one ring); the ring is as deep as the shared-memory budget allows.
+// and `empty` barriers and `depth` record stages.  Consumer warps per CTA:
+// enough that the CTAs about cover the SMs once (all chains of an SM then
+// share one ring), or the tuned count.  CTAs per SM: as many as the work
+// needs and the registers allow (the persistent kernel queues the rest); the
+// ring is as deep as the shared memory left to each of them.  For a batch the
+// shape covers the largest problem.
+int ctas_per_sm(int precision, const LaunchShape &sh, int kv, bool batch)
+{
+    return precision == ASM_FP64 ? sweep_ctas_per_sm_f64(sh, kv, batch) : sweep_ctas_per_sm_f32(sh, kv, batch);
+}
+
 template <class T>
-bool plan_pipeline(SweepParams<T> &sp, int max_rec, int chains)
+bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long long total_warps, int kv,
+                bool batch, int want_consumers)
 {
     constexpr int kSMs = 152;
-    const int TW = 32 / sp.S;
-    const long long warps = (chains + TW - 1) / TW;
-    int consumers = (int)std::min<long long>(8, std::max<long long>(1, (warps + kSMs - 1) / kSMs));
+    const int TW = 32 / S;
+    const int prec = sizeof(T) == 8 ? ASM_FP64 : ASM_MIXED;
+    sh.S = S;
+    sh.cpad = round_up_int(std::max(max_np, 1), 32);
+    sh.mpad = round_up_int(std::max(max_M, 1), 32);
+    int consumers = want_consumers > 0
+                        ? want_consumers
+                        : (int)std::min<long long>(8, std::max<long long>(1, (total_warps + kSMs - 1) / kSMs));
     if (const char *e = std::getenv("ASM_CONSUMERS_PER_CTA")) {   // tuning override
         const int c = std::atoi(e);
         if (c >= 1 && c <= 8) consumers = c;
     }
-    const long long ctas = (warps + consumers - 1) / consumers;
-    const int ctas_per_sm = (int)std::max<long long>(1, (ctas + kSMs - 1) / kSMs);
-    const size_t budget = std::min<size_t>(220 * 1024 / ctas_per_sm, 227 * 1024);
-    sp.stage_bytes = (int)align_up((size_t)max_rec * sizeof(T), 128);
+    sh.stage_bytes = (int)align_up((size_t)max_rec * sizeof(T), 128);
     auto fixed = [&](int c) {
-        return align_up((size_t)c * TW * (2 * sp.cpad + sp.mpad) * sizeof(T), 128) + 256;
+        return align_up((size_t)c * TW * (2 * sh.cpad + sh.mpad) * sizeof(T), 128) + 256;
     };
-    int depth = 16;
+    int max_depth = 16;
     if (const char *e = std::getenv("ASM_RING_DEPTH")) {            // tuning override
         const int d = std::atoi(e);
-        if (d >= 2 && d <= 16) depth = d;
+        if (d >= 2 && d <= 16) max_depth = d;
     }
-    while (depth > 2 && fixed(consumers) + (size_t)depth * sp.stage_bytes > budget) --depth;
-    while (consumers > 1 && fixed(consumers) + (size_t)depth * sp.stage_bytes > budget) --consumers;
-    if (fixed(consumers) + (size_t)depth * sp.stage_bytes > 227 * 1024) return false;
-    sp.consumers = consumers;
-    sp.depth = depth;
-    sp.off_full = (int)align_up((size_t)consumers * TW * (2 * sp.cpad + sp.mpad) * sizeof(T), 128);
-    sp.off_empty = sp.off_full + 128;
-    sp.off_stages = sp.off_full + 256;
-    return true;
+    for (; consumers >= 1; --consumers) {
+        LaunchShape probe = sh;   // no dynamic shared memory: the register limit alone
+        probe.consumers = consumers;
+        probe.depth = 0;
+        probe.off_stages = 0;
+        const int by_regs = std::max(1, ctas_per_sm(prec, probe, kv, batch));
+        const long long ctas = (total_warps + consumers - 1) / consumers;
+        const int per_sm = (int)std::min<long long>(by_regs, std::max<long long>(1, (ctas + kSMs - 1) / kSMs));
+        const size_t budget = std::min<size_t>(220 * 1024 / per_sm, 227 * 1024);
+        int depth = max_depth;
+        while (depth > 2 && fixed(consumers) + (size_t)depth * sh.stage_bytes > budget) --depth;
+        if (fixed(consumers) + (size_t)depth * sh.stage_bytes <= budget || consumers == 1) {
+            if (fixed(consumers) + (size_t)depth * sh.stage_bytes > 227 * 1024) return false;
+            sh.consumers = consumers;
+            sh.depth = depth;
+            sh.off_full = (int)align_up((size_t)consumers * TW * (2 * sh.cpad + sh.mpad) * sizeof(T), 128);
+            sh.off_empty = sh.off_full + 128;
+            sh.off_stages = sh.off_full + 256;
+            return true;
+        }
+    }
+    return false;
 }
 
 int pick_kv(int max_nb, int vec, int S, int kmax)
@@ -769,52 +911,179 @@ int moment_update(asm_problem *p, const WsLayout &L, int chains)
     return ASM_OK;
 }
 
-template <class T>
-int run_sweeps(asm_problem *p, const WsLayout &L, int chains, long long s_begin, long long s_end,
-               long long burn_abs)
+// Dynamic shared memory of a refresh kernel (one FP64 chain state).
+template <class K>
+int refresh_smem(K kernel, size_t bytes)
 {
-    const PrecBuffers &b = sizeof(T) == 8 ? p->b64 : p->b32;
-    SweepParams<T> sp = make_params<T>(p, b, L, chains);
-    sp.burn_in = burn_abs;
+    if (bytes > 227 * 1024) return ASM_ERR_TOO_LARGE;
+    if (bytes > 48 * 1024 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    return ASM_OK;
+}
+
+void drop_graph(asm_problem *h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->gkey = asm_problem::GraphKey{};
+}
+
+// Sweeps [s_begin, s_end) of every chain of every problem of handle h in
+// persistent launches of the sweep kernel, one per refresh period (or
+// snapshot interval), each followed where due by the FP64 refresh of all
+// residuals.  Whole refresh periods are replays of one CUDA graph (advance
+// the range, sweep, refresh) unless launches are timed, snapshots are taken
+// or the caller's stream is being captured.
+template <class T>
+int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long long burn_abs)
+{
+    std::vector<asm_problem *> us = units_of(h);
+    const RunLayout RL = run_layout(h, chains, h->precision);
+    char *base = (char *)h->ws_all;
+    std::vector<SweepParams<T>> probs;
+    int max_rec = 0, max_np = 1, max_M = 1, max_nb = 1, max_N = 1;
+    for (asm_problem *u : us) {
+        const WsLayout L = ws_layout(u, chains, h->precision);
+        probs.push_back(make_params<T>(u, sizeof(T) == 8 ? u->b64 : u->b32, L, chains));
+        max_rec = std::max(max_rec, u->max_rec);
+        max_np = std::max(max_np, u->max_np);
+        max_M = std::max(max_M, u->M);
+        max_nb = std::max(max_nb, u->max_nb);
+        max_N = std::max(max_N, u->N);
+    }
+    const int S = h->team;
     const int vec = 16 / (int)sizeof(T);
-    const int kv = pick_kv(p->max_nb, vec, sp.S, sizeof(T) == 8 ? kMaxKvF64 : kMaxKvF32);
+    const int kv = pick_kv(max_nb, vec, S, sizeof(T) == 8 ? kMaxKvF64 : kMaxKvF32);
     if (kv < 0) return ASM_ERR_TOO_LARGE;
-    if (!plan_pipeline(sp, p->max_rec, chains)) return ASM_ERR_TOO_LARGE;
-    char *ws = (char *)p->ws;
+    const int TW = 32 / S;
+    const long long warps_per_unit = (chains + TW - 1) / TW;
+    const bool batch = !h->kids.empty();
+    LaunchShape sh{};
+    if (!plan_shape<T>(sh, S, max_rec, max_np, max_M, warps_per_unit * (long long)us.size(), kv, batch,
+                       h->tuned_consumers))
+        return ASM_ERR_TOO_LARGE;
+    // work items, the costliest problems first (a longest-first queue)
+    std::vector<int> order(us.size());
+    for (size_t k = 0; k < us.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long long)us[a]->N * us[a]->max_nb > (long long)us[b]->N * us[b]->max_nb;
+    });
+    std::vector<WorkItem> items;
+    const int groups = (int)((warps_per_unit + sh.consumers - 1) / sh.consumers);
+    for (int k : order)
+        for (int g = 0; g < groups; ++g) items.push_back(WorkItem{k, g});
+    sh.n_items = (int)items.size();
+    const int per_sm = ctas_per_sm(h->precision, sh, kv, batch);
+    if (per_sm <= 0) return ASM_ERR_CUDA;
+    const int ctas = (int)std::min<long long>(sh.n_items, 152LL * per_sm);
+    h->last_team = sh.S;
+    h->last_consumers = sh.consumers;
+    h->last_ctas = ctas;
+    h->last_items = sh.n_items;
+    const size_t rsmem = sizeof(double) * (size_t)max_N;
+    if (const int rc = refresh_smem(refresh_all_kernel<T>, rsmem); rc != ASM_OK) return rc;
+    SweepParams<T> *d_probs = (SweepParams<T> *)(base + RL.probs);
+    WorkItem *d_items = (WorkItem *)(base + RL.items);
+    RunCtrl *ctrl = (RunCtrl *)(base + RL.ctrl);
+    if (cudaMemcpyAsync(d_probs, probs.data(), sizeof(SweepParams<T>) * probs.size(), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    const unsigned n_refresh = (unsigned)(us.size() * chains);
+    const SweepParams<T> &p0 = probs[0];   // a single problem's parameters travel by value
+    auto sweep = [&](cudaStream_t st) {
+        if constexpr (sizeof(T) == 8) return launch_sweeps_f64(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
+        else return launch_sweeps_f32(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
+    };
+    auto refresh = [&](cudaStream_t st) {
+        refresh_all_kernel<T><<<n_refresh, 128, rsmem, st>>>(d_probs, chains, 1);
+        return cudaGetLastError();
+    };
+    bool graphs = !h->timing && !h->moments && !h->no_graph;
+    if (graphs) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) return ASM_ERR_CUDA;
+        graphs = cs == cudaStreamCaptureStatusNone;
+    }
     long long s = s_begin;
     while (s < s_end) {
+        const long long whole = (s % kRefreshPeriod == 0) ? (s_end - s) / kRefreshPeriod : 0;
+        if (graphs && whole >= 2) {
+            asm_problem::GraphKey key;
+            key.ws_all = h->ws_all;
+            key.chains = chains;
+            key.precision = h->precision;
+            key.kv = kv;
+            key.ctas = ctas;
+            key.S = sh.S;
+            key.consumers = sh.consumers;
+            key.depth = sh.depth;
+            key.n_items = sh.n_items;
+            key.refresh_smem = rsmem;
+            key.seed = p0.seed;   // by value in a single problem's launch
+            key.problem_id = p0.problem_id;
+            key.chain_offset = p0.chain_offset;
+            if (!h->gexec || !(h->gkey == key)) {
+                drop_graph(h);
+                if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+                    return ASM_ERR_CUDA;
+                if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                    return ASM_ERR_CUDA;
+                ctrl_kernel<<<1, 1, 0, h->cap_stream>>>(ctrl, 0, 0, 0, 1);
+                cudaError_t e = cudaGetLastError();
+                if (e == cudaSuccess) e = sweep(h->cap_stream);
+                if (e == cudaSuccess) e = refresh(h->cap_stream);
+                cudaGraph_t graph = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+                if (e == cudaSuccess && e2 == cudaSuccess)
+                    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (e != cudaSuccess || e2 != cudaSuccess) {
+                    h->gexec = nullptr;
+                    return ASM_ERR_CUDA;
+                }
+                h->gkey = key;
+            }
+            // the first replay advances [s - P, s) to [s, s + P)
+            ctrl_kernel<<<1, 1, 0, h->stream>>>(ctrl, s - kRefreshPeriod, kRefreshPeriod, burn_abs, 0);
+            if (cudaGetLastError() != cudaSuccess) return ASM_ERR_CUDA;
+            for (long long i = 0; i < whole; ++i)
+                if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) return ASM_ERR_CUDA;
+            h->sweep_launches += whole;
+            h->other_launches += 1 + 2 * whole;
+            h->graph_replays += whole;
+            s += whole * kRefreshPeriod;
+            continue;
+        }
         long long seg = std::min<long long>(kRefreshPeriod - (s % kRefreshPeriod), s_end - s);
-        if (p->moments) {   // also stop at the next snapshot of the kept sweeps
+        if (h->moments) {   // also stop at the next snapshot of the kept sweeps
             const long long k = s < burn_abs ? -1 : (s - burn_abs) / ASM_SNAPSHOT_EVERY;
             const long long next = burn_abs + (k + 1) * ASM_SNAPSHOT_EVERY;
             seg = std::min(seg, next - s);
         }
-        sp.sweep0 = s;
-        sp.nsweeps = seg;
+        ctrl_kernel<<<1, 1, 0, h->stream>>>(ctrl, s, seg, burn_abs, 0);
+        if (cudaGetLastError() != cudaSuccess) return ASM_ERR_CUDA;
+        ++h->other_launches;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (p->timing) {
-            if (p->ev_used + 2 > 4096 && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
-            e0 = next_event(p);
-            e1 = next_event(p);
-            if (!e0 || !e1 || cudaEventRecord(e0, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
+        if (h->timing) {
+            if (h->ev_used + 2 > 4096 && drain_events(h) != ASM_OK) return ASM_ERR_CUDA;
+            e0 = next_event(h);
+            e1 = next_event(h);
+            if (!e0 || !e1 || cudaEventRecord(e0, h->stream) != cudaSuccess) return ASM_ERR_CUDA;
         }
-        cudaError_t e;
-        if constexpr (sizeof(T) == 8) e = launch_sweeps_f64(sp, kv, p->stream);
-        else e = launch_sweeps_f32(sp, kv, p->stream);
-        if (e != cudaSuccess) return ASM_ERR_CUDA;
-        if (p->timing && cudaEventRecord(e1, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
-        ++p->sweep_launches;
+        if (sweep(h->stream) != cudaSuccess) return ASM_ERR_CUDA;
+        if (h->timing && cudaEventRecord(e1, h->stream) != cudaSuccess) return ASM_ERR_CUDA;
+        ++h->sweep_launches;
         s += seg;
-        if (p->moments && s > burn_abs && (s - burn_abs) % ASM_SNAPSHOT_EVERY == 0) {
-            const int rc = moment_update<T>(p, L, chains);
+        if (h->moments && s > burn_abs && (s - burn_abs) % ASM_SNAPSHOT_EVERY == 0) {
+            const int rc = moment_update<T>(us[0], ws_layout(us[0], chains, h->precision), chains);
             if (rc != ASM_OK) return rc;
         }
         if (s % kRefreshPeriod == 0) {
-            refresh_kernel<T><<<chains, 128, sizeof(double) * p->N, p->stream>>>(
-                p->M, p->N, p->d_KtT, p->d_gt, sp.F, sp.ldF, sp.R, sp.ldR, (double *)(ws + L.chi2),
-                sp.counters, 1);
-            if (cudaGetLastError() != cudaSuccess) return ASM_ERR_CUDA;
-            ++p->other_launches;
+            if (refresh(h->stream) != cudaSuccess) return ASM_ERR_CUDA;
+            ++h->other_launches;
         }
     }
     return ASM_OK;
@@ -834,6 +1103,7 @@ int init_chains(asm_problem *p, const WsLayout &L, int chains)
     // snapshot moments of the backward pass start at zero
     if (cudaMemsetAsync(ws + L.Sff, 0, L.Gtmp - L.Sff, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
     p->nsnap = 0;
+    if (const int rc = refresh_smem(refresh_kernel<T>, sizeof(double) * p->N); rc != ASM_OK) return rc;
     refresh_kernel<T><<<chains, 128, sizeof(double) * p->N, p->stream>>>(
         p->M, p->N, p->d_KtT, p->d_gt, (const T *)(ws + L.F), L.ldF, (T *)(ws + L.R), L.ldR,
         (double *)(ws + L.chi2), (Counters *)(ws + L.counters), 0);
@@ -1051,47 +1321,196 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
 size_t asm_workspace_bytes(const asm_problem *p, int chains, int precision)
 {
     if (!p || chains < 1 || (precision != ASM_FP64 && precision != ASM_MIXED)) return 0;
-    return ws_layout(p, chains, precision).total;
+    return run_layout(p, chains, precision).total;
 }
+
+int asm_problem_count(const asm_problem *p)
+{
+    if (!p) return ASM_ERR_ARG;
+    return p->kids.empty() ? 1 : (int)p->kids.size();
+}
+
+namespace {
+// Point every problem of handle p at its section of the caller's workspace.
+void bind_workspace(asm_problem *p, void *ws_all, size_t bytes, const RunLayout &RL, cudaStream_t stream)
+{
+    p->ws_all = ws_all;
+    p->ws_bytes = bytes;
+    p->stream = stream;
+    const auto us = units_of(p);
+    for (size_t k = 0; k < us.size(); ++k) {
+        us[k]->ws_all = ws_all;
+        us[k]->ws = (char *)ws_all + RL.unit[k];
+        us[k]->ws_bytes = bytes;
+        us[k]->stream = stream;
+    }
+}
+
+// Fresh chains for every problem of handle p.
+int start_chains(asm_problem *p, int chains, int precision, uint64_t seed, bool moments)
+{
+    const auto us = units_of(p);
+    const bool batch = !p->kids.empty();
+    p->moments = moments;
+    p->chains = chains;
+    p->precision = precision;
+    p->seed = seed;
+    p->problem_id = p->next_problem_id;
+    p->chain_offset = p->next_chain_offset;
+    p->sweeps_done = 0;
+    p->kept = 0;
+    p->sweep_launches = p->other_launches = p->timed_launches = 0;
+    p->graph_replays = 0;
+    p->timed_ms = 0.0;
+    for (size_t k = 0; k < us.size(); ++k) {
+        asm_problem *u = us[k];
+        if (batch) {
+            u->moments = false;
+            u->chains = chains;
+            u->precision = precision;
+            u->seed = seed;
+            u->problem_id = p->problem_id + (unsigned long long)k;   // batch problem k: problem id P + k
+            u->chain_offset = p->chain_offset;
+            u->sweeps_done = 0;
+            u->kept = 0;
+            u->sweep_launches = u->other_launches = u->timed_launches = 0;
+        }
+        const WsLayout L = ws_layout(u, chains, precision);
+        const int rc = precision == ASM_FP64 ? init_chains<double>(u, L, chains) : init_chains<float>(u, L, chains);
+        if (rc != ASM_OK) return rc;
+        u->have_run = true;
+    }
+    p->have_run = true;
+    return ASM_OK;
+}
+
+// Sums the device counters of every problem of handle p (synchronises).
+int read_counters_all(asm_problem *p, Counters *c)
+{
+    *c = Counters{};
+    for (asm_problem *u : units_of(p)) {
+        Counters cu{};
+        if (cudaMemcpyAsync(&cu, u->ws, sizeof(cu), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+            cudaStreamSynchronize(p->stream) != cudaSuccess)
+            return ASM_ERR_CUDA;
+        c->degenerate += cu.degenerate;
+        c->zero_mode += cu.zero_mode;
+        c->tail_capped += cu.tail_capped;
+        c->nonfinite += cu.nonfinite;
+        c->timeouts += cu.timeouts;
+        c->drift_bits = std::max(c->drift_bits, cu.drift_bits);   // non-negative doubles order like their bits
+    }
+    return ASM_OK;
+}
+
+void finish_sweeps(asm_problem *p, long long s1, long long kept_add)
+{
+    p->sweeps_done = s1;
+    p->kept += kept_add;
+    if (!p->kids.empty())
+        for (asm_problem *u : p->kids) {
+            u->sweeps_done = s1;
+            u->kept += kept_add;
+        }
+}
+}  // namespace
 
 int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t seed, int precision,
                uint32_t flags, void *d_workspace, size_t workspace_bytes, void *stream)
 {
     if (!p || chains < 1 || burn_in < 0 || sweeps < 0) return ASM_ERR_ARG;
     if (precision != ASM_FP64 && precision != ASM_MIXED) return ASM_ERR_ARG;
-    const WsLayout L = ws_layout(p, chains, precision);
-    if (!d_workspace || workspace_bytes < L.total || ((uintptr_t)d_workspace & 255)) return ASM_ERR_WORKSPACE;
+    const bool moments = (flags & ASM_SAMPLE_MOMENTS) != 0;
+    if (moments && !p->kids.empty()) return ASM_ERR_ARG;   // backward moments: single problems
+    const RunLayout RL = run_layout(p, chains, precision);
+    if (!d_workspace || workspace_bytes < RL.total || ((uintptr_t)d_workspace & 255)) return ASM_ERR_WORKSPACE;
     const bool cont = (flags & ASM_SAMPLE_CONTINUE) != 0;
-    if (cont && (!p->have_run || p->chains != chains || p->precision != precision || p->ws != d_workspace ||
+    if (cont && (!p->have_run || p->chains != chains || p->precision != precision || p->ws_all != d_workspace ||
                  p->seed != seed))
         return ASM_ERR_STATE;
     if (p->ev_used && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
-    p->stream = (cudaStream_t)stream;
+    bind_workspace(p, d_workspace, workspace_bytes, RL, (cudaStream_t)stream);
     p->timing = (flags & ASM_SAMPLE_TIMING) != 0;
-    p->ws = d_workspace;
-    p->ws_bytes = workspace_bytes;
     int rc;
     if (!cont) {
-        p->moments = (flags & ASM_SAMPLE_MOMENTS) != 0;
-        p->chains = chains;
-        p->precision = precision;
-        p->seed = seed;
-        p->problem_id = p->next_problem_id;
-        p->chain_offset = p->next_chain_offset;
-        p->sweeps_done = 0;
-        p->kept = 0;
-        p->sweep_launches = p->other_launches = p->timed_launches = 0;
-        p->timed_ms = 0.0;
-        rc = precision == ASM_FP64 ? init_chains<double>(p, L, chains) : init_chains<float>(p, L, chains);
+        rc = start_chains(p, chains, precision, seed, moments);
         if (rc != ASM_OK) return rc;
-        p->have_run = true;
     }
     const long long s0 = p->sweeps_done, s1 = s0 + burn_in + sweeps, burn_abs = s0 + burn_in;
-    rc = precision == ASM_FP64 ? run_sweeps<double>(p, L, chains, s0, s1, burn_abs)
-                               : run_sweeps<float>(p, L, chains, s0, s1, burn_abs);
+    rc = precision == ASM_FP64 ? run_all<double>(p, chains, s0, s1, burn_abs)
+                               : run_all<float>(p, chains, s0, s1, burn_abs);
     if (rc != ASM_OK) return rc;
-    p->sweeps_done = s1;
-    p->kept += sweeps;
+    finish_sweeps(p, s1, sweeps);
+    return ASM_OK;
+}
+
+int asm_tune(asm_problem *p, int chains, int precision, void *d_workspace, size_t workspace_bytes, void *stream,
+             int *team_out, int *consumers_out)
+{
+    if (!p || chains < 1 || (precision != ASM_FP64 && precision != ASM_MIXED)) return ASM_ERR_ARG;
+    const RunLayout RL = run_layout(p, chains, precision);
+    if (!d_workspace || workspace_bytes < RL.total || ((uintptr_t)d_workspace & 255)) return ASM_ERR_WORKSPACE;
+    if (p->ev_used && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
+    bind_workspace(p, d_workspace, workspace_bytes, RL, (cudaStream_t)stream);
+    const int team0 = p->team, cons0 = p->tuned_consumers;
+    const bool timing0 = p->timing;
+    p->timing = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return ASM_ERR_CUDA;
+    }
+    int best_team = team0, best_cons = cons0, rc = ASM_OK;
+    float best = 0.f;
+    bool any = false;
+    const int teams[] = {32, 16, 8};
+    const int conss[] = {0, 2, 4, 6, 7, 8};   // 0: the built-in heuristic
+    for (int S : teams) {
+        for (int c : conss) {
+            p->team = S;
+            p->tuned_consumers = c;
+            // fresh chains, one sweep to warm up, then the timed sweeps
+            rc = start_chains(p, chains, precision, 0x74756e65ull, false);
+            if (rc != ASM_OK) break;
+            int r = precision == ASM_FP64 ? run_all<double>(p, chains, 0, 1, 0) : run_all<float>(p, chains, 0, 1, 0);
+            if (r == ASM_ERR_TOO_LARGE) continue;   // this shape does not fit the problems
+            if (r != ASM_OK) { rc = r; break; }
+            if (cudaEventRecord(e0, p->stream) != cudaSuccess) { rc = ASM_ERR_CUDA; break; }
+            r = precision == ASM_FP64 ? run_all<double>(p, chains, 1, 4, 0) : run_all<float>(p, chains, 1, 4, 0);
+            if (r != ASM_OK) { rc = r; break; }
+            float ms = 0.f;
+            if (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = ASM_ERR_CUDA;
+                break;
+            }
+            Counters c0{};
+            if (read_counters_all(p, &c0) != ASM_OK) { rc = ASM_ERR_CUDA; break; }
+            if (c0.timeouts) { rc = ASM_ERR_TIMEOUT; break; }
+            if (!any || ms < best) {
+                best = ms;
+                best_team = S;
+                best_cons = c;
+                any = true;
+            }
+        }
+        if (rc != ASM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->timing = timing0;
+    // the workspace now holds trial chains: the next asm_sample starts afresh
+    p->have_run = false;
+    for (asm_problem *u : p->kids) u->have_run = false;
+    if (rc != ASM_OK || !any) {
+        p->team = team0;
+        p->tuned_consumers = cons0;
+        return rc != ASM_OK ? rc : ASM_ERR_TOO_LARGE;
+    }
+    p->team = best_team;
+    p->tuned_consumers = best_cons;
+    if (team_out) *team_out = best_team;
+    if (consumers_out) *consumers_out = best_cons;
     return ASM_OK;
 }
 
@@ -1106,9 +1525,17 @@ int read_counters(asm_problem *p, Counters *c)
 }
 }  // namespace
 
+int asm_average_at(asm_problem *p, int k, double *mean_A, double *sem_A, double *ess, double *mean_fbar)
+{
+    if (!p || k < 0 || k >= asm_problem_count(p)) return ASM_ERR_ARG;
+    if (p->kids.empty()) return asm_average(p, mean_A, sem_A, ess, mean_fbar);
+    return asm_average(p->kids[(size_t)k], mean_A, sem_A, ess, mean_fbar);
+}
+
 int asm_average(asm_problem *p, double *mean_A, double *sem_A, double *ess, double *mean_fbar)
 {
     if (!p) return ASM_ERR_ARG;
+    if (!p->kids.empty()) return ASM_ERR_ARG;   // a batch: asm_average_at
     if (!p->have_run || p->kept < 1) return ASM_ERR_STATE;
     {
         Counters c{};
@@ -1146,6 +1573,7 @@ int asm_average(asm_problem *p, double *mean_A, double *sem_A, double *ess, doub
 int asm_backward(asm_problem *p, const double *v, double *grad_G, double *grad_theta)
 {
     if (!p || !v) return ASM_ERR_ARG;
+    if (!p->kids.empty()) return ASM_ERR_ARG;
     if (!p->have_run || !p->moments || p->nsnap < 2) return ASM_ERR_STATE;
     if (grad_G && !p->d_L) return ASM_ERR_STATE;
     if (grad_theta && p->P == 0) return ASM_ERR_ARG;
@@ -1192,6 +1620,7 @@ int asm_backward(asm_problem *p, const double *v, double *grad_G, double *grad_t
 int asm_chain_state(asm_problem *p, double *f, double *chi2)
 {
     if (!p) return ASM_ERR_ARG;
+    if (!p->kids.empty()) return ASM_ERR_ARG;
     if (!p->have_run) return ASM_ERR_STATE;
     {
         Counters c{};
@@ -1233,9 +1662,7 @@ int asm_status(asm_problem *p, asm_stats *out)
     if (!p->have_run) return ASM_ERR_STATE;
     if (drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
     Counters c{};
-    if (cudaMemcpyAsync(&c, p->ws, sizeof(c), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
-        cudaStreamSynchronize(p->stream) != cudaSuccess)
-        return ASM_ERR_CUDA;
+    if (read_counters_all(p, &c) != ASM_OK) return ASM_ERR_CUDA;
     out->chains = p->chains;
     out->sweeps_done = p->sweeps_done;
     out->kept_sweeps = p->kept;
@@ -1249,9 +1676,16 @@ int asm_status(asm_problem *p, asm_stats *out)
     out->max_resync_drift = drift;
     out->sweep_launches = p->sweep_launches;
     out->other_launches = p->other_launches;
+    if (!p->kids.empty())
+        for (asm_problem *u : p->kids) out->other_launches += u->other_launches;
     out->timed_launches = p->timed_launches;
     out->sweep_kernel_ms = p->timed_ms;
     out->timeouts = (int64_t)c.timeouts;
+    out->graph_replays = p->graph_replays;
+    out->team_lanes = p->last_team;
+    out->consumers_per_cta = p->last_consumers;
+    out->ctas = p->last_ctas;
+    out->work_items = p->last_items;
     return ASM_OK;
 }
 
@@ -1262,37 +1696,26 @@ int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, ui
     if (!p || chains < 1 || burn_in < 0 || sweeps < 1 || !d_mean_fbar || !d_sem2_fbar || !d_m2_fbar)
         return ASM_ERR_ARG;
     if (precision != ASM_FP64 && precision != ASM_MIXED) return ASM_ERR_ARG;
-    const WsLayout L = ws_layout(p, chains, precision);
-    if (L.total > ASM_NOALLOC_SCRATCH_BYTES) return ASM_ERR_TOO_LARGE;
+    if (!p->kids.empty()) return ASM_ERR_ARG;
+    const RunLayout RL = run_layout(p, chains, precision);
+    if (RL.total > ASM_NOALLOC_SCRATCH_BYTES) return ASM_ERR_TOO_LARGE;
     void *scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc != ASM_OK) return rc;
     if (p->ev_used && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
-    p->stream = (cudaStream_t)stream;
+    bind_workspace(p, scratch, ASM_NOALLOC_SCRATCH_BYTES, RL, (cudaStream_t)stream);
     p->timing = false;
-    p->ws = scratch;
-    p->ws_bytes = ASM_NOALLOC_SCRATCH_BYTES;
-    p->moments = false;
-    p->chains = chains;
-    p->precision = precision;
-    p->seed = seed;
-    p->problem_id = p->next_problem_id;
-    p->chain_offset = p->next_chain_offset;
-    p->sweeps_done = 0;
-    p->kept = 0;
-    p->sweep_launches = p->other_launches = p->timed_launches = 0;
-    p->timed_ms = 0.0;
     // counters, sums and residuals are zeroed and the chains re-started here
-    rc = precision == ASM_FP64 ? init_chains<double>(p, L, chains) : init_chains<float>(p, L, chains);
+    rc = start_chains(p, chains, precision, seed, false);
     if (rc != ASM_OK) return rc;
-    p->have_run = true;
     const long long s1 = (long long)burn_in + sweeps;
-    rc = precision == ASM_FP64 ? run_sweeps<double>(p, L, chains, 0, s1, burn_in)
-                               : run_sweeps<float>(p, L, chains, 0, s1, burn_in);
+    p->no_graph = true;   // graph instantiation allocates
+    rc = precision == ASM_FP64 ? run_all<double>(p, chains, 0, s1, burn_in) : run_all<float>(p, chains, 0, s1, burn_in);
+    p->no_graph = false;
     if (rc != ASM_OK) return rc;
-    p->sweeps_done = s1;
-    p->kept = sweeps;
-    const char *ws = (const char *)scratch;
+    finish_sweeps(p, s1, sweeps);
+    const WsLayout L = ws_layout(p, chains, precision);
+    const char *ws = (const char *)p->ws;
     reduce_kernel<<<(p->N + 127) / 128, 128, 0, p->stream>>>((const double *)(ws + L.S1),
                                                              (const double *)(ws + L.S2), chains, p->N,
                                                              (double)sweeps, d_mean_fbar, d_sem2_fbar, d_m2_fbar);
@@ -1320,7 +1743,7 @@ constexpr uint64_t kCheckpointMagic = 0x41534d434b505431ull;   // "ASMCKPT1"
 
 int asm_checkpoint(asm_problem *p, void *host_buf, size_t *bytes)
 {
-    if (!p || !bytes) return ASM_ERR_ARG;
+    if (!p || !bytes || !p->kids.empty()) return ASM_ERR_ARG;
     if (!p->have_run) return ASM_ERR_STATE;
     const WsLayout L = ws_layout(p, p->chains, p->precision);
     const size_t need = sizeof(CheckpointHeader) + L.total;
@@ -1343,23 +1766,22 @@ int asm_checkpoint(asm_problem *p, void *host_buf, size_t *bytes)
 int asm_restore(asm_problem *p, const void *host_buf, size_t bytes, void *d_workspace, size_t workspace_bytes,
                 void *stream)
 {
-    if (!p || !host_buf || bytes < sizeof(CheckpointHeader)) return ASM_ERR_ARG;
+    if (!p || !host_buf || bytes < sizeof(CheckpointHeader) || !p->kids.empty()) return ASM_ERR_ARG;
     CheckpointHeader h;
     std::memcpy(&h, host_buf, sizeof(h));
     if (h.magic != kCheckpointMagic || h.version != 1) return ASM_ERR_ARG;
     if (h.M != p->M || h.N != p->N) return ASM_ERR_SHAPE;
     if (h.precision != ASM_FP64 && h.precision != ASM_MIXED) return ASM_ERR_ARG;
     const WsLayout L = ws_layout(p, (int)h.chains, (int)h.precision);
+    const RunLayout RL = run_layout(p, (int)h.chains, (int)h.precision);
     if ((int64_t)L.total != h.ws_bytes || bytes < sizeof(h) + L.total) return ASM_ERR_ARG;
-    if (!d_workspace || workspace_bytes < L.total || ((uintptr_t)d_workspace & 255)) return ASM_ERR_WORKSPACE;
+    if (!d_workspace || workspace_bytes < RL.total || ((uintptr_t)d_workspace & 255)) return ASM_ERR_WORKSPACE;
     if (p->ev_used && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
-    p->stream = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(d_workspace, (const char *)host_buf + sizeof(h), L.total, cudaMemcpyHostToDevice,
+    bind_workspace(p, d_workspace, workspace_bytes, RL, (cudaStream_t)stream);
+    if (cudaMemcpyAsync(p->ws, (const char *)host_buf + sizeof(h), L.total, cudaMemcpyHostToDevice,
                         p->stream) != cudaSuccess ||
         cudaStreamSynchronize(p->stream) != cudaSuccess)
         return ASM_ERR_CUDA;
-    p->ws = d_workspace;
-    p->ws_bytes = workspace_bytes;
     p->chains = (int)h.chains;
     p->precision = (int)h.precision;
     p->seed = h.seed;
@@ -1374,9 +1796,33 @@ int asm_restore(asm_problem *p, const void *host_buf, size_t bytes, void *d_work
     return ASM_OK;
 }
 
+int asm_setup_batch(int n, const asm_desc *d, asm_problem **out)
+{
+    if (!out || !d || n < 1) return ASM_ERR_ARG;
+    *out = nullptr;
+    asm_problem *b = new (std::nothrow) asm_problem;
+    if (!b) return ASM_ERR_ARG;
+    for (int k = 0; k < n; ++k) {
+        asm_problem *u = nullptr;
+        const int rc = asm_setup(&d[k], &u);
+        if (rc != ASM_OK) {
+            asm_destroy(b);
+            return rc;
+        }
+        b->kids.push_back(u);
+        b->M = std::max(b->M, u->M);
+        b->N = std::max(b->N, u->N);
+    }
+    b->team = b->kids[0]->team;
+    *out = b;
+    return ASM_OK;
+}
+
 void asm_destroy(asm_problem *p)
 {
     if (!p) return;
+    for (asm_problem *u : p->kids) asm_destroy(u);
+    p->kids.clear();
     void *ptrs[] = {p->d_level_first, p->d_level_nblocks, p->d_blocks, p->d_KtT, p->d_gt, p->d_L,
                     p->d_Kth64, p->d_Kth32, p->d_w, p->d_dw, p->d_vjp};
     if (p->blas) cublasDestroy(p->blas);
@@ -1385,6 +1831,8 @@ void asm_destroy(asm_problem *p)
     free_prec(p->b64);
     free_prec(p->b32);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    drop_graph(p);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     delete p;
 }
 

@@ -450,13 +450,35 @@ __device__ __forceinline__ void fused_pass_smem(T (&f)[KV][VecOf<T>::n], T delta
 // Position in the stream of moves of a launch (sweep, level, block, mode).
 // --------------------------------------------------------------------------
 struct MoveCursor {
-    long long s;            // sweep
+    long long s, s_end;     // sweep, end of the launch's range
     int bi, j;              // block within the level, mode within the block
     int nb;                 // blocks of the level
     const BlockDesc *bd;    // blocks of the level
     BlockDesc B;            // the current block (a copy)
     bool done;
 };
+
+// The launch's sweep range, read from the device control block.
+struct SweepRange {
+    long long sweep0, nsweeps, burn_in;
+};
+
+// A warp's position in the record ring: records seen (g), stage and phase
+// (kept incrementally: no division per move).
+struct RingPos {
+    unsigned g;             // records in this launch (< 2^32: one launch is at most 64 sweeps)
+    int slot;
+    unsigned phase;
+};
+
+__device__ __forceinline__ void ring_next(RingPos &r, int depth)
+{
+    ++r.g;
+    if (++r.slot == depth) {
+        r.slot = 0;
+        r.phase ^= 1u;
+    }
+}
 
 __device__ __forceinline__ int level_of_sweep(long long s, unsigned long long seed, unsigned long long pid,
                                               int n_levels)
@@ -487,7 +509,7 @@ __device__ __forceinline__ void cursor_advance(MoveCursor &c, const SweepParams<
         c.B = c.bd[c.bi];
         return;
     }
-    if (++c.s >= p.sweep0 + p.nsweeps) {
+    if (++c.s >= c.s_end) {
         c.done = true;
         return;
     }
@@ -500,88 +522,74 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 }
 
 // --------------------------------------------------------------------------
-// The producer warp: one bulk copy per move of the launch into the ring,
-// after every consumer warp has released the slot's previous record.
+// The producer warp: one bulk copy per move of the item into the ring, after
+// every consumer warp has released the slot's previous record.  The ring
+// position runs on across the CTA's items.
 // --------------------------------------------------------------------------
 template <class T>
-__device__ __forceinline__ void produce(const SweepParams<T> &p, unsigned long long *full,
-                                        unsigned long long *empty, unsigned char *stages, Counters *cnt)
+__device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchShape &sh, const SweepRange &rg,
+                                        unsigned long long *full, unsigned long long *empty,
+                                        unsigned char *stages, RingPos &rp, bool &failed)
 {
-    if ((threadIdx.x & 31) != 0 || p.nsweeps <= 0) return;
-    const int D = p.depth;
+    if ((threadIdx.x & 31) != 0 || rg.nsweeps <= 0 || failed) return;
+    const int D = sh.depth;
     MoveCursor c;
-    c.s = p.sweep0;
+    c.s = rg.sweep0;
+    c.s_end = rg.sweep0 + rg.nsweeps;
     c.done = false;
     cursor_start_sweep(c, p);
-    unsigned long long g = 0;
-    bool failed = false;
-    for (; !c.done; ++g) {
-        const int slot = (int)(g % (unsigned long long)D);
-        if (g >= (unsigned long long)D) {
-            const unsigned parity = (unsigned)(((g / (unsigned long long)D) - 1ull) & 1ull);
-            if (!mbar_wait(empty + slot, parity, kWaitLimit)) {
-                failed = true;
-                break;
-            }
+    const unsigned g0 = rp.g;
+    while (!c.done) {
+        // the slot's previous record (phase ^ 1) must have been released
+        if (rp.g >= (unsigned)D && !mbar_wait(empty + rp.slot, rp.phase ^ 1u, kWaitLimit)) {
+            failed = true;
+            break;
         }
         const unsigned bytes = (unsigned)(c.B.recstride * sizeof(T));
-        mbar_expect_tx(full + slot, bytes);
-        bulk_g2s(stages + (size_t)slot * p.stage_bytes, p.pd.rec + c.B.offRec + (size_t)c.j * c.B.recstride,
-                 bytes, full + slot);
+        mbar_expect_tx(full + rp.slot, bytes);
+        bulk_g2s(stages + (size_t)rp.slot * sh.stage_bytes, p.pd.rec + c.B.offRec + (size_t)c.j * c.B.recstride,
+                 bytes, full + rp.slot);
+        ring_next(rp, D);
         cursor_advance(c, p);
     }
     if (failed) {
         // the copies already issued must land before the CTA may exit
-        for (unsigned long long k = g > (unsigned long long)D ? g - D : 0; k < g; ++k)
-            mbar_wait(full + (k % (unsigned long long)D), (unsigned)((k / (unsigned long long)D) & 1ull),
-                      kWaitLimit);
-        atomicAdd(&cnt->timeouts, 1ull);
+        const unsigned g = rp.g;
+        const unsigned from = g > g0 + (unsigned)D ? g - D : g0;
+        for (unsigned k = from; k < g; ++k)
+            mbar_wait(full + (k % (unsigned)D), (k / (unsigned)D) & 1u, kWaitLimit);
+        atomicAdd(&p.counters->timeouts, 1ull);
     }
 }
 
 // --------------------------------------------------------------------------
-// the sweep kernel: sweeps [sweep0, sweep0 + nsweeps) of every chain.
-// Warps 0 .. consumers-1 run chains; warp `consumers` produces the records.
+// A consumer warp: its team(s) of S lanes run the chains of chain group
+// `group` (consumers x 32/S chains) of problem p for the launch's sweeps.
 // --------------------------------------------------------------------------
 template <class T, int KV>
-__global__ void __launch_bounds__(288) sweep_kernel(const SweepParams<T> p)
+__device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchShape &sh, const SweepRange &rg,
+                                        int group, unsigned char *smem_raw, unsigned long long *full,
+                                        unsigned long long *empty, unsigned char *stages, RingPos &rp,
+                                        bool &failed)
 {
     constexpr int VEC = VecOf<T>::n;
+    if (failed) return;
     const int lane = threadIdx.x & 31;
     const int wcta = threadIdx.x >> 5;
-    const int D = p.depth;
-
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem_raw + p.off_full);
-    unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem_raw + p.off_empty);
-    unsigned char *stages = smem_raw + p.off_stages;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < D; ++i) {
-            mbar_init(full + i, 1);
-            mbar_init(empty + i, (unsigned)p.consumers);
-        }
-        fence_mbar_init();
-        fence_proxy_async_smem();
-    }
-    __syncthreads();
-    if (wcta == p.consumers) {
-        produce(p, full, empty, stages, p.counters);
-        return;
-    }
-
-    const int S = p.S;
+    const int D = sh.depth;
+    const int S = sh.S;
     const int TW = 32 / S;
     const int team = lane / S;
     const int sl = lane - team * S;
     const int team_base = team * S;
-    const long long gwarp = (long long)blockIdx.x * p.consumers + wcta;
+    const long long gwarp = (long long)group * sh.consumers + wcta;
     const long long q_raw = gwarp * TW + team;
     const bool active = q_raw < p.chains;
     const long long q = active ? q_raw : (long long)p.chains - 1;  // idle teams shadow a real chain, write nothing
 
-    T *csm = reinterpret_cast<T *>(smem_raw) + (size_t)(wcta * TW + team) * (2 * p.cpad + p.mpad);
-    T *wsm = csm + p.cpad;
-    T *rsm = wsm + p.cpad;
+    T *csm = reinterpret_cast<T *>(smem_raw) + (size_t)(wcta * TW + team) * (2 * sh.cpad + sh.mpad);
+    T *wsm = csm + sh.cpad;
+    T *rsm = wsm + sh.cpad;
     T *Rq = p.R + (size_t)q * p.ldR;
     for (int m = sl; m < p.M; m += S) rsm[m] = Rq[m];
     T *Fq = p.F + (size_t)q * p.ldF;
@@ -593,13 +601,11 @@ __global__ void __launch_bounds__(288) sweep_kernel(const SweepParams<T> p)
     unsigned long long n_deg = 0, n_zero = 0, n_bad = 0;
     int capped = 0;
     unsigned long long rw0 = 0, rw1 = 0, rw2 = 0, rw3 = 0;
-    unsigned long long g = 0;   // move sequence number (warp-uniform)
-    bool failed = false;
-
-    for (long long s = p.sweep0; s < p.sweep0 + p.nsweeps && !failed; ++s) {
+    const long long s_end = rg.sweep0 + rg.nsweeps;
+    for (long long s = rg.sweep0; s < s_end && !failed; ++s) {
         // level of this sweep: same for every chain of the problem (Sec. IV.C)
         const int level = level_of_sweep(s, p.seed, p.problem_id, p.n_levels);
-        const bool keep = s >= p.burn_in;
+        const bool keep = s >= rg.burn_in;
         long long win = -1;  // first move index covered by this lane's Philox words
         const int nb = p.level_nblocks[level];
         const BlockDesc *bd = p.blocks + p.level_first[level];
@@ -642,8 +648,8 @@ __global__ void __launch_bounds__(288) sweep_kernel(const SweepParams<T> p)
                 if (win < 0 || t >= win + 4 * S) {
                     win = (long long)(t / (4 * S)) * (4 * S);
                     unsigned long long c0 = (unsigned long long)(win >> 2) + (unsigned long long)sl;
-                    unsigned long long c1 = (unsigned long long)s,
-                                       c2 = (unsigned long long)q + p.chain_offset, c3 = p.problem_id;
+                    unsigned long long c1 = (unsigned long long)s, c2 = (unsigned long long)q + p.chain_offset,
+                                       c3 = p.problem_id;
                     philox4x64_10(c0, c1, c2, c3, p.seed, 0ull);
                     rw0 = c0; rw1 = c1; rw2 = c2; rw3 = c3;
                 }
@@ -653,14 +659,12 @@ __global__ void __launch_bounds__(288) sweep_kernel(const SweepParams<T> p)
                 const unsigned long long word = __shfl_sync(0xffffffffu, mine, team_base + src);
                 const T u = uniform_from<T>(word);
                 // this move's record
-                const int slot = (int)(g % (unsigned long long)D);
-                const unsigned parity = (unsigned)((g / (unsigned long long)D) & 1ull);
-                const bool ok = mbar_wait_ready(full + slot, parity, kWaitLimit);
+                const bool ok = mbar_wait_ready(full + rp.slot, rp.phase, kWaitLimit);
                 if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
                     failed = true;
                     break;
                 }
-                const T *st = reinterpret_cast<const T *>(stages + (size_t)slot * p.stage_bytes);
+                const T *st = reinterpret_cast<const T *>(stages + (size_t)rp.slot * sh.stage_bytes);
                 const T dj = st[3 * B.rs], ij = st[3 * B.rs + 1];
 
                 team_bounds(lo, hi, S, team_base);
@@ -682,8 +686,8 @@ __global__ void __launch_bounds__(288) sweep_kernel(const SweepParams<T> p)
                 fused_pass_smem<T, KV>(f, delta, st, st + B.rs, st + 2 * B.rs, kcnt, sl, S, lo, hi);
                 // release the record to the producer (one arrival per warp)
                 __syncwarp();
-                if (lane == 0) mbar_arrive(empty + slot);
-                ++g;
+                if (lane == 0) mbar_arrive(empty + rp.slot);
+                ring_next(rp, D);
             }
             if (failed) break;
             __syncwarp();
@@ -735,18 +739,110 @@ __global__ void __launch_bounds__(288) sweep_kernel(const SweepParams<T> p)
     }
 }
 
-template <class T, int KV>
-cudaError_t launch_sweep_kernel(const SweepParams<T> &p, cudaStream_t stream)
+// --------------------------------------------------------------------------
+// the persistent sweep kernel: the sweeps [ctrl->sweep0, + ctrl->nsweeps) of
+// every work item (problem, chain group).  Warps 0 .. consumers-1 run chains;
+// warp `consumers` produces the move records.  CTAs pull items from
+// ctrl->queue.  One problem (BATCH = false): its parameters are the launch's
+// grid constant p0.  Several: each item's parameters are copied from probs
+// into shared memory.
+// --------------------------------------------------------------------------
+template <class T, int KV, bool BATCH>
+__global__ void __launch_bounds__(288) sweep_kernel(const __grid_constant__ SweepParams<T> p0,
+                                                    const SweepParams<T> *__restrict__ probs,
+                                                    const WorkItem *__restrict__ items, RunCtrl *ctrl,
+                                                    const __grid_constant__ LaunchShape shape)
 {
-    const int TW = 32 / p.S;
-    const long long warps = (p.chains + TW - 1) / TW;
-    const long long ctas = (warps + p.consumers - 1) / p.consumers;
-    const size_t smem = (size_t)p.off_stages + (size_t)p.depth * p.stage_bytes;
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    __shared__ SweepParams<T> sp;
+    __shared__ SweepRange rg;
+    __shared__ int s_item;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem_raw + shape.off_full);
+    unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem_raw + shape.off_empty);
+    unsigned char *stages = smem_raw + shape.off_stages;
+    const int wcta = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < shape.depth; ++i) {
+            mbar_init(full + i, 1);
+            mbar_init(empty + i, (unsigned)shape.consumers);
+        }
+        fence_mbar_init();
+        fence_proxy_async_smem();
+        rg.sweep0 = ctrl->sweep0;
+        rg.nsweeps = ctrl->nsweeps;
+        rg.burn_in = ctrl->burn_in;
+    }
+    RingPos rp{0u, 0, 0u};
+    bool failed = false;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ctrl->queue, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= shape.n_items) break;
+        const WorkItem w = items[it];
+        if constexpr (BATCH) {
+            if (threadIdx.x == 0) sp = probs[w.problem];
+            __syncthreads();
+        }
+        const SweepParams<T> &p = BATCH ? sp : p0;
+        if (wcta == shape.consumers)
+            produce(p, shape, rg, full, empty, stages, rp, failed);
+        else
+            consume<T, KV>(p, shape, rg, w.group, smem_raw, full, empty, stages, rp, failed);
+        __syncthreads();   // the item is finished before sp and s_item change
+    }
+}
+
+template <class T, int KV, bool BATCH>
+cudaError_t launch_sweep_kernel(const SweepParams<T> &p0, const SweepParams<T> *probs, const WorkItem *items,
+                                RunCtrl *ctrl, const LaunchShape &shape, int ctas, cudaStream_t stream)
+{
+    const size_t smem = (size_t)shape.off_stages + (size_t)shape.depth * shape.stage_bytes;
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, KV, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    sweep_kernel<T, KV><<<(unsigned)ctas, 32 * (p.consumers + 1), smem, stream>>>(p);
+    sweep_kernel<T, KV, BATCH><<<(unsigned)ctas, 32 * (shape.consumers + 1), smem, stream>>>(p0, probs, items, ctrl,
+                                                                                             shape);
     return cudaGetLastError();
 }
+
+template <class T, int KV, bool BATCH>
+int sweep_ctas_per_sm(const LaunchShape &shape)
+{
+    const size_t smem = (size_t)shape.off_stages + (size_t)shape.depth * shape.stage_bytes;
+    if (cudaFuncSetAttribute(sweep_kernel<T, KV, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, KV, BATCH>, 32 * (shape.consumers + 1),
+                                                      smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+// dispatch over the register tile (kv) and the batch flag
+template <class T, int... KVs>
+struct SweepDispatch {
+    static cudaError_t launch(const SweepParams<T> &p0, const SweepParams<T> *probs, const WorkItem *items,
+                              RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch, int ctas, cudaStream_t s)
+    {
+        cudaError_t e = cudaErrorInvalidValue;
+        ((kv == KVs ? (e = batch ? launch_sweep_kernel<T, KVs, true>(p0, probs, items, ctrl, shape, ctas, s)
+                                 : launch_sweep_kernel<T, KVs, false>(p0, probs, items, ctrl, shape, ctas, s),
+                       0)
+                    : 0),
+         ...);
+        return e;
+    }
+    static int per_sm(const LaunchShape &shape, int kv, bool batch)
+    {
+        int n = 0;
+        ((kv == KVs ? (n = batch ? sweep_ctas_per_sm<T, KVs, true>(shape) : sweep_ctas_per_sm<T, KVs, false>(shape),
+                       0)
+                    : 0),
+         ...);
+        return n;
+    }
+};
 
 }  // namespace asmgb

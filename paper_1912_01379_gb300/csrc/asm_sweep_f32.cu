@@ -3,16 +3,17 @@
 
 namespace asmgb {
 
-cudaError_t launch_sweeps_f32(const SweepParams<float> &p, int kv, cudaStream_t s)
+using DispatchF32 = SweepDispatch<float, 1, 2, 4, 8, 16>;
+
+cudaError_t launch_sweeps_f32(const SweepParams<float> &p0, const SweepParams<float> *probs, const WorkItem *items,
+                              RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch, int ctas, cudaStream_t s)
 {
-    switch (kv) {
-    case 1: return launch_sweep_kernel<float, 1>(p, s);
-    case 2: return launch_sweep_kernel<float, 2>(p, s);
-    case 4: return launch_sweep_kernel<float, 4>(p, s);
-    case 8: return launch_sweep_kernel<float, 8>(p, s);
-    case 16: return launch_sweep_kernel<float, 16>(p, s);
-    default: return cudaErrorInvalidValue;
-    }
+    return DispatchF32::launch(p0, probs, items, ctrl, shape, kv, batch, ctas, s);
+}
+
+int sweep_ctas_per_sm_f32(const LaunchShape &shape, int kv, bool batch)
+{
+    return DispatchF32::per_sm(shape, kv, batch);
 }
 
 }  // namespace asmgb

@@ -1,19 +1,19 @@
-// FP64 chain state (the plain FP64 path): instantiations of the sweep kernel.
+// FP64 chain state: instantiations of the sweep kernel.
 #include "asm_sweep.cuh"
 
 namespace asmgb {
 
-cudaError_t launch_sweeps_f64(const SweepParams<double> &p, int kv, cudaStream_t s)
+using DispatchF64 = SweepDispatch<double, 1, 2, 4, 8, 16, 32>;
+
+cudaError_t launch_sweeps_f64(const SweepParams<double> &p0, const SweepParams<double> *probs, const WorkItem *items,
+                              RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch, int ctas, cudaStream_t s)
 {
-    switch (kv) {
-    case 1: return launch_sweep_kernel<double, 1>(p, s);
-    case 2: return launch_sweep_kernel<double, 2>(p, s);
-    case 4: return launch_sweep_kernel<double, 4>(p, s);
-    case 8: return launch_sweep_kernel<double, 8>(p, s);
-    case 16: return launch_sweep_kernel<double, 16>(p, s);
-    case 32: return launch_sweep_kernel<double, 32>(p, s);
-    default: return cudaErrorInvalidValue;
-    }
+    return DispatchF64::launch(p0, probs, items, ctrl, shape, kv, batch, ctas, s);
+}
+
+int sweep_ctas_per_sm_f64(const LaunchShape &shape, int kv, bool batch)
+{
+    return DispatchF64::per_sm(shape, kv, batch);
 }
 
 }  // namespace asmgb
