@@ -52,6 +52,7 @@ enum { ASM_FP64 = 0, ASM_MIXED = 1 };   /* precision of asm_sample */
 #define ASM_SAMPLE_CONTINUE 1u   /* keep the chains of the previous call and go on */
 #define ASM_SAMPLE_TIMING 2u     /* record CUDA events around every sweep-kernel launch */
 #define ASM_SAMPLE_MOMENTS 4u    /* accumulate the snapshot moments asm_backward needs */
+#define ASM_SAMPLE_REFRESH_FP64 8u  /* ASM_MIXED: refresh residuals on FP64 CUDA cores, not 3xTF32 tensor cores */
 #define ASM_SNAPSHOT_EVERY 8     /* kept sweeps between snapshots of all chains */
 
 typedef struct asm_problem asm_problem;  /* opaque, library-owned */
@@ -110,6 +111,7 @@ typedef struct {
     double sweep_kernel_ms;     /* summed event-timed duration of those launches */
     int64_t timeouts;           /* bounded device waits that gave up (0 in a valid run) */
     int64_t graph_replays;      /* refresh periods run as replays of the handle's CUDA graph */
+    int64_t tc_refreshes;       /* residual refreshes run on the tensor cores (3xTF32) */
     int32_t team_lanes;         /* lanes per chain of the last sweep launch */
     int32_t consumers_per_cta;  /* chain warps per CTA of the last sweep launch */
     int32_t ctas;               /* CTAs of the last sweep launch (persistent) */
@@ -163,8 +165,12 @@ size_t asm_workspace_bytes(const asm_problem *p, int chains, int precision);
  * Philox4x64-10 uniform keyed by (seed, problem id, global chain id, sweep,
  * move); see asm_set_stream_ids.
  * Sweeps after burn-in are accumulated into FP64 sums of fbar and fbar^2.
- * precision: ASM_FP64 runs the chain state in FP64; ASM_MIXED runs it in FP32
- * with FP64 accumulators and an FP64 residual refresh every 64 sweeps.
+ * precision: ASM_FP64 runs the chain state in FP64 with an FP64 residual
+ * refresh every 64 sweeps; ASM_MIXED runs it in FP32 with FP64 accumulators and
+ * refreshes r~ = g~ - K~ f every 64 sweeps as one tensor-core GEMM over all
+ * chains in split precision (3xTF32: f_hi K_hi + f_hi K_lo + f_lo K_hi, FP32
+ * accumulation; error ~2^-21 |K~||f| per term), the difference, chi^2 and the
+ * drift in FP64 (ASM_SAMPLE_REFRESH_FP64: on FP64 CUDA cores instead).
  * flags: ASM_SAMPLE_CONTINUE continues the chains of the previous call on the
  * same workspace (same chains, seed and precision) without resetting the sums;
  * otherwise chains start from the flat default-model scale fit.

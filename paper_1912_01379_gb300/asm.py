@@ -20,6 +20,7 @@ ASM_MIXED = 1
 ASM_SAMPLE_CONTINUE = 1
 ASM_SAMPLE_TIMING = 2
 ASM_SAMPLE_MOMENTS = 4
+ASM_SAMPLE_REFRESH_FP64 = 8
 ASM_SNAPSHOT_EVERY = 8
 
 _dp = ct.POINTER(ct.c_double)
@@ -41,7 +42,8 @@ class asm_stats(ct.Structure):
                 ("nonfinite_moves", ct.c_int64), ("max_resync_drift", ct.c_double),
                 ("sweep_launches", ct.c_int64), ("other_launches", ct.c_int64),
                 ("timed_launches", ct.c_int64), ("sweep_kernel_ms", ct.c_double),
-                ("timeouts", ct.c_int64), ("graph_replays", ct.c_int64), ("team_lanes", ct.c_int32),
+                ("timeouts", ct.c_int64), ("graph_replays", ct.c_int64), ("tc_refreshes", ct.c_int64),
+                ("team_lanes", ct.c_int32),
                 ("consumers_per_cta", ct.c_int32), ("ctas", ct.c_int32), ("work_items", ct.c_int32)]
 
 
@@ -192,13 +194,13 @@ class _Handle:
         return torch, workspace
 
     def sample(self, chains, burn_in, sweeps, seed, precision=ASM_MIXED, cont=False, stream=None,
-               workspace=None, timing=False, moments=False):
+               workspace=None, timing=False, moments=False, refresh_fp64=False):
         """asm_sample on a torch workspace (allocated here unless given) and the
         current torch stream (or `stream`)."""
         torch, workspace = self._workspace(chains, precision, workspace)
         s = stream if stream is not None else torch.cuda.current_stream()
         flags = ((ASM_SAMPLE_CONTINUE if cont else 0) | (ASM_SAMPLE_TIMING if timing else 0) |
-                 (ASM_SAMPLE_MOMENTS if moments else 0))
+                 (ASM_SAMPLE_MOMENTS if moments else 0) | (ASM_SAMPLE_REFRESH_FP64 if refresh_fp64 else 0))
         _check(load().asm_sample(self._h, chains, burn_in, sweeps, ct.c_uint64(seed), precision, flags,
                                  ct.c_void_p(workspace.data_ptr()), workspace.numel(),
                                  ct.c_void_p(s.cuda_stream)), "asm_sample")

@@ -1,6 +1,6 @@
 """In-tree build of the CUDA library libasm_gb300.so for sm_103a (nvcc, no cmake).
 
-The three translation units compile in parallel; the result lands in
+The translation units compile in parallel; the result lands in
 paper_1912_01379_gb300/_build/ (git-ignored) and is rebuilt only when a source
 or header is newer than it.
 """
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libasm_gb300.so")
-UNITS = ["asm_lib.cu", "asm_sweep_f32.cu", "asm_sweep_f64.cu"]
+UNITS = ["asm_lib.cu", "asm_sweep_f32.cu", "asm_sweep_f64.cu", "asm_refresh_tc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
          "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

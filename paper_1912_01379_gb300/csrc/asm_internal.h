@@ -66,6 +66,10 @@ struct SweepParams {
     const double *KtT, *gt;           // whitened kernel (N x M) and data
     double *chi2;                     // chains
     double f0;                        // starting value of every fbar_n
+    // whitened kernel split into TF32 high and low parts (M x ldK FP32 each) for
+    // the tensor-core refresh of the mixed path
+    const float *Khi, *Klo;
+    int ldK;
 };
 
 // What every problem of one launch shares: the CTA shape and the
@@ -109,6 +113,14 @@ cudaError_t launch_sweeps_f32(const SweepParams<float> &p0, const SweepParams<fl
 cudaError_t launch_sweeps_f64(const SweepParams<double> &p0, const SweepParams<double> *probs,
                               const WorkItem *items, RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch,
                               int ctas, cudaStream_t s);
+// Tensor-core residual refresh of the mixed path (asm_refresh_tc.cu): grid of
+// (chain tiles of 128) x n_problems CTAs; max_bn = the largest refresh_tc_bn(M).
+cudaError_t launch_refresh_tc(const SweepParams<float> *probs, int n_problems, int chains, int max_bn, bool track_drift,
+                              cudaStream_t s);
+int refresh_tc_bn(int M);                  // MMA N of a problem's M_tau tiles
+size_t refresh_tc_smem(int max_bn);        // dynamic shared memory of one CTA
+constexpr int kRefreshTcLdK = 32;          // ldK is a multiple of this (one k-tile)
+cudaError_t launch_split_k(const double *KtT, int M, int N, int ldK, float *Khi, float *Klo, cudaStream_t s);
 // CTAs of the persistent kernel that fit one SM at this shape (shared memory included).
 int sweep_ctas_per_sm_f32(const LaunchShape &shape, int kv, bool batch);
 int sweep_ctas_per_sm_f64(const LaunchShape &shape, int kv, bool batch);

@@ -310,6 +310,8 @@ struct asm_problem {
     int *d_level_first = nullptr, *d_level_nblocks = nullptr;
     BlockDesc *d_blocks = nullptr;
     double *d_KtT = nullptr, *d_gt = nullptr;
+    float *d_Khi = nullptr, *d_Klo = nullptr;   // K~ split into TF32 high/low parts (M x ldK)
+    int ldK = 0;
     // backward pass
     int P = 0;
     double *d_L = nullptr;                 // Cholesky factor of C (M x M, column-major lower)
@@ -352,7 +354,8 @@ struct asm_problem {
                    problem_id == o.problem_id && chain_offset == o.chain_offset;
         }
     } gkey;
-    long long graph_replays = 0;
+    long long graph_replays = 0, tc_refreshes = 0;
+    bool refresh_fp64 = false;   // mixed path: FP64 CUDA-core refresh instead of the tensor cores
     int last_team = 0, last_consumers = 0, last_ctas = 0, last_items = 0;   // shape of the last sweep launch
     bool no_graph = false;    // direct launches only (the allocation-free entry point)
     // launch bookkeeping
@@ -763,6 +766,9 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.pd.meta = (const T *)b.meta;
     sp.pd.rec = (const T *)b.rec;
     sp.KtT = p->d_KtT;
+    sp.Khi = p->d_Khi;
+    sp.Klo = p->d_Klo;
+    sp.ldK = p->ldK;
     sp.gt = p->d_gt;
     sp.chi2 = (double *)(ws + L.chi2);
     sp.f0 = p->f0;
@@ -983,6 +989,11 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
     h->last_items = sh.n_items;
     const size_t rsmem = sizeof(double) * (size_t)max_N;
     if (const int rc = refresh_smem(refresh_all_kernel<T>, rsmem); rc != ASM_OK) return rc;
+    // the mixed path refreshes on the tensor cores (3xTF32) unless asked for FP64 CUDA cores
+    const bool tc = sizeof(T) == 4 && !h->refresh_fp64;
+    int max_bn = 16;
+    for (asm_problem *u : us) max_bn = std::max(max_bn, refresh_tc_bn(u->M));
+    if (tc && refresh_tc_smem(max_bn) > 227 * 1024) return ASM_ERR_TOO_LARGE;
     SweepParams<T> *d_probs = (SweepParams<T> *)(base + RL.probs);
     WorkItem *d_items = (WorkItem *)(base + RL.items);
     RunCtrl *ctrl = (RunCtrl *)(base + RL.ctrl);
@@ -998,6 +1009,11 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
         else return launch_sweeps_f32(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
     };
     auto refresh = [&](cudaStream_t st) {
+        if constexpr (sizeof(T) == 4) {
+            if (tc) {
+                return launch_refresh_tc(d_probs, (int)us.size(), chains, max_bn, true, st);
+            }
+        }
         refresh_all_kernel<T><<<n_refresh, 128, rsmem, st>>>(d_probs, chains, 1);
         return cudaGetLastError();
     };
@@ -1021,7 +1037,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             key.consumers = sh.consumers;
             key.depth = sh.depth;
             key.n_items = sh.n_items;
-            key.refresh_smem = rsmem;
+            key.refresh_smem = tc ? refresh_tc_smem(max_bn) + 1 : rsmem;
             key.seed = p0.seed;   // by value in a single problem's launch
             key.problem_id = p0.problem_id;
             key.chain_offset = p0.chain_offset;
@@ -1054,6 +1070,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             h->sweep_launches += whole;
             h->other_launches += 1 + 2 * whole;
             h->graph_replays += whole;
+            if (tc) h->tc_refreshes += whole;
             s += whole * kRefreshPeriod;
             continue;
         }
@@ -1084,6 +1101,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
         if (s % kRefreshPeriod == 0) {
             if (refresh(h->stream) != cudaSuccess) return ASM_ERR_CUDA;
             ++h->other_launches;
+            if (tc) ++h->tc_refreshes;
         }
     }
     return ASM_OK;
@@ -1309,6 +1327,16 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
         asm_destroy(p);
         return rc;
     }
+    // K~ in TF32 high/low parts for the tensor-core refresh
+    p->ldK = round_up_int(N, kRefreshTcLdK);
+    const size_t nk = (size_t)M * p->ldK;
+    if (cudaMalloc((void **)&p->d_Khi, nk * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void **)&p->d_Klo, nk * sizeof(float)) != cudaSuccess ||
+        launch_split_k(p->d_KtT, M, N, p->ldK, p->d_Khi, p->d_Klo, nullptr) != cudaSuccess ||
+        cudaStreamSynchronize(nullptr) != cudaSuccess) {
+        asm_destroy(p);
+        return ASM_ERR_CUDA;
+    }
     const char *team = std::getenv("ASM_TEAM_LANES");
     if (team) {
         const int t = std::atoi(team);
@@ -1361,6 +1389,7 @@ int start_chains(asm_problem *p, int chains, int precision, uint64_t seed, bool 
     p->kept = 0;
     p->sweep_launches = p->other_launches = p->timed_launches = 0;
     p->graph_replays = 0;
+    p->tc_refreshes = 0;
     p->timed_ms = 0.0;
     for (size_t k = 0; k < us.size(); ++k) {
         asm_problem *u = us[k];
@@ -1431,6 +1460,7 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
     if (p->ev_used && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
     bind_workspace(p, d_workspace, workspace_bytes, RL, (cudaStream_t)stream);
     p->timing = (flags & ASM_SAMPLE_TIMING) != 0;
+    p->refresh_fp64 = (flags & ASM_SAMPLE_REFRESH_FP64) != 0;
     int rc;
     if (!cont) {
         rc = start_chains(p, chains, precision, seed, moments);
@@ -1682,6 +1712,7 @@ int asm_status(asm_problem *p, asm_stats *out)
     out->sweep_kernel_ms = p->timed_ms;
     out->timeouts = (int64_t)c.timeouts;
     out->graph_replays = p->graph_replays;
+    out->tc_refreshes = p->tc_refreshes;
     out->team_lanes = p->last_team;
     out->consumers_per_cta = p->last_consumers;
     out->ctas = p->last_ctas;
@@ -1823,7 +1854,7 @@ void asm_destroy(asm_problem *p)
     if (!p) return;
     for (asm_problem *u : p->kids) asm_destroy(u);
     p->kids.clear();
-    void *ptrs[] = {p->d_level_first, p->d_level_nblocks, p->d_blocks, p->d_KtT, p->d_gt, p->d_L,
+    void *ptrs[] = {p->d_level_first, p->d_level_nblocks, p->d_blocks, p->d_KtT, p->d_gt, p->d_Khi, p->d_Klo, p->d_L,
                     p->d_Kth64, p->d_Kth32, p->d_w, p->d_dw, p->d_vjp};
     if (p->blas) cublasDestroy(p->blas);
     for (void *x : ptrs)
