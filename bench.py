@@ -11,7 +11,9 @@ the mixed FP32/FP64 path.  `value` = chain-mode updates per second
 (chains x sweeps x N_omega per step, burn-in included) with the inputs resident
 on the device; `e2e` runs asm_setup from host arrays + asm_sample + asm_average
 (device->host results) per step.  The plain FP64 path and ESS/s of <A(omega)>
-are reported beside it.
+are reported beside it, and, as side measurements outside the timed region,
+the batching workload (256 uneven problems in one handle) and the grid-size
+sweep (N_omega 250..2000, 8192 chains), each in both paths.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -55,6 +57,10 @@ def _args():
     ap.add_argument("--fp64-sweeps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-sweeps", type=int, default=256,
+                    help="sweeps of the batching side measurement (0: skip)")
+    ap.add_argument("--grid-sweeps", type=int, default=64,
+                    help="sweeps per N_omega of the grid-size side measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -185,6 +191,68 @@ def cpu_baseline(p, seconds_target=12.0):
     return {"value": upd / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{chains} chains x {sweeps} sweeps of the same workload (FP64 oracle, OpenMP over chains)",
             "seconds": dt}
+
+
+def _spec(p):
+    return dict(K=p.K, G=p.G, C=p.C, levels=p.levels, w=p.w)
+
+
+def _timed(torch, stream, fn):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def batch_side(args, asm, torch, stream):
+    """Batching workload (256 problems with uneven N_omega, N_tau and blocks, 64
+    chains each) in one handle: persistent launches replayed from the CUDA
+    graph, launch shape picked by asm_tune; mixed path and plain FP64 path."""
+    probs = W.batch_problems()
+    chains = probs[0].chains
+    b = asm.Batch([_spec(p) for p in probs])
+    sumN = sum(p.N for p in probs)
+    out = {"workload": "batch_256_problems_Nomega100-1000_Ntau50-200_64chains", "problems": len(probs),
+           "chains_per_problem": chains, "sweeps": args.batch_sweeps}
+    for prec, key, sweeps in ((asm.ASM_MIXED, "mixed", args.batch_sweeps),
+                              (asm.ASM_FP64, "fp64", max(64, args.batch_sweeps // 4))):
+        team, cons = b.tune(chains, precision=prec)
+        b.sample(chains, 0, 1, 11, precision=prec)   # warm-up launch
+        t = _timed(torch, stream, lambda: b.sample(chains, 0, sweeps, 12, precision=prec))
+        st = b.status()
+        out[key] = {"updates_per_s": chains * sweeps * sumN / t, "seconds": t, "sweeps": sweeps,
+                    "team_lanes": st["team_lanes"], "consumers_per_cta": st["consumers_per_cta"],
+                    "ctas": st["ctas"], "work_items": st["work_items"], "graph_replays": st["graph_replays"],
+                    "timeouts": st["timeouts"]}
+    out["speedup_mixed_vs_fp64"] = out["mixed"]["updates_per_s"] / out["fp64"]["updates_per_s"]
+    return out
+
+
+def grid_side(args, asm, torch, stream):
+    """Grid-size sweep (N_tau = 400, beta = 50, 16 blocks, 8192 chains) at
+    N_omega in {250, 500, 1000, 2000}: mixed path (tensor-core refresh) and
+    plain FP64 path rates over one refresh period."""
+    rows = []
+    for N in (250, 500, 1000, 2000):
+        p = W.grid_sweep_problem(N, "uniform")
+        gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w)
+        chains = p.chains
+        row = {"N_omega": N, "N_tau": p.M, "chains": chains}
+        for prec, key, sweeps in ((asm.ASM_MIXED, "mixed", args.grid_sweeps),
+                                  (asm.ASM_FP64, "fp64", max(2, args.grid_sweeps // 8))):
+            gp.sample(chains, 0, 1, 21, precision=prec)
+            t = _timed(torch, stream, lambda: gp.sample(chains, 0, sweeps, 22, precision=prec))
+            st = gp.status()
+            row[key] = {"updates_per_s": chains * sweeps * N / t, "sweeps": sweeps,
+                        "tc_refreshes": st["tc_refreshes"], "timeouts": st["timeouts"]}
+        row["speedup_mixed_vs_fp64"] = row["mixed"]["updates_per_s"] / row["fp64"]["updates_per_s"]
+        rows.append(row)
+        del gp
+    return {"workload": "grid_sweep_fermionic_b50_Ntau400_uniform_16blocks_8192chains", "rows": rows}
 
 
 def run_reference(args):
@@ -324,6 +392,9 @@ def main():
         e2e = {"value": ws * updates_per_step / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": nst}
 
+    batch = batch_side(args, asm, torch, stream) if (args.batch_sweeps > 0 and rank == 0) else None
+    grid = grid_side(args, asm, torch, stream) if (args.grid_sweeps > 0 and rank == 0) else None
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p)
@@ -347,6 +418,8 @@ def main():
                          "kernel": "sweep_kernel<float>", "avg_launch_ms": sweep_ms / max(sweep_launches, 1)},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "batch": batch,
+            "grid_sweep": grid,
             "gpu_launches": int(sweep_launches + other_launches + args.steps),
             "clocks": clocks,
         }
