@@ -775,7 +775,8 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     return sp;
 }
 
-// Shared memory of the sweep kernel: per team c, w and r~; the ring's `full`
+// Shared memory of the sweep kernel: per team c, w, r~ and the uniforms of a
+// window of 4S moves; the ring's `full`
 // and `empty` barriers and `depth` record stages.  Consumer warps per CTA:
 // enough that the CTAs about cover the SMs once (all chains of an SM then
 // share one ring), or the tuned count.  CTAs per SM: as many as the work
@@ -806,7 +807,7 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
     }
     sh.stage_bytes = (int)align_up((size_t)max_rec * sizeof(T), 128);
     auto fixed = [&](int c) {
-        return align_up((size_t)c * TW * (2 * sh.cpad + sh.mpad) * sizeof(T), 128) + 256;
+        return align_up((size_t)c * TW * (2 * sh.cpad + sh.mpad + 4 * S) * sizeof(T), 128) + 256;
     };
     int max_depth = 16;
     if (const char *e = std::getenv("ASM_RING_DEPTH")) {            // tuning override
@@ -828,7 +829,7 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
             if (fixed(consumers) + (size_t)depth * sh.stage_bytes > 227 * 1024) return false;
             sh.consumers = consumers;
             sh.depth = depth;
-            sh.off_full = (int)align_up((size_t)consumers * TW * (2 * sh.cpad + sh.mpad) * sizeof(T), 128);
+            sh.off_full = (int)align_up((size_t)consumers * TW * (2 * sh.cpad + sh.mpad + 4 * S) * sizeof(T), 128);
             sh.off_empty = sh.off_full + 128;
             sh.off_stages = sh.off_full + 256;
             return true;

@@ -86,13 +86,19 @@ __device__ __forceinline__ double m_abs(double x) { return fabs(x); }
 __device__ __forceinline__ float m_abs(float x) { return fabsf(x); }
 
 template <class T> struct TailTraits;
+// far: with both standardized bounds beyond +-far, Phi(a) and 1 - Phi(b) are
+// below half an ulp of the smallest uniform (2^-53 resp. 2^-24), so
+// (1-u) Phi(a) + u Phi(b) rounds to u: Phi(-12) = 1.8e-33 < 2^-107 and
+// Phi(-10) = 7.6e-24 < 2^-49.
 template <> struct TailTraits<double> {
     static constexpr double tol = 1e-14;
     static constexpr int nmax = 40;
+    static constexpr double far = 12.0;
 };
 template <> struct TailTraits<float> {
     static constexpr float tol = 2e-6f;
     static constexpr int nmax = 16;
+    static constexpr float far = 10.0f;
 };
 
 // x ~ N(0,1) restricted to [a, b], 0 <= a < b <= inf, by Q(x) = (1-u)Q(a) + uQ(b).
@@ -215,6 +221,10 @@ __device__ __forceinline__ T tn_step(T c, T d, T invd, T lo, T hi, T u, int &cap
         delta = lo + invd * right_tail(a, b, u, capped);
     } else if (b <= T(0)) {
         delta = hi - invd * right_tail(-b, -a, T(1) - u, capped);
+    } else if (a < -TailTraits<T>::far && b > TailTraits<T>::far) {
+        // the truncation is below the resolution of u: the untruncated inverse CDF
+        const T x = u <= T(0.5) ? m_phiinv(u) : -m_phiinv(T(1) - u);
+        delta = (x + c) * invd;
     } else {
         const T p = (T(1) - u) * m_phi(a) + u * m_phi(b);
         T x;
@@ -367,23 +377,16 @@ __device__ __forceinline__ void fence_mbar_init()
 
 constexpr int kWaitLimit = 1 << 22;
 
-// Team-wide max of lo and min of hi.  FP32: one redux instruction each on
-// integer keys that order like the floats (neither value is ever NaN).
-// FP64: a butterfly of shuffles.
-__device__ __forceinline__ int ord_key(float f)
-{
-    const int i = __float_as_int(f);
-    return i >= 0 ? i : i ^ 0x7fffffff;
-}
-__device__ __forceinline__ float ord_val(int k)
-{
-    return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff);
-}
+// Team-wide max of lo and min of hi.  FP32: one floating-point redux
+// instruction each (neither value is ever NaN).  FP64: a butterfly of shuffles.
 __device__ __forceinline__ void team_bounds(float &lo, float &hi, int S, int team_base)
 {
     const unsigned mask = S == 32 ? 0xffffffffu : (((1u << S) - 1u) << team_base);
-    lo = ord_val(__reduce_max_sync(mask, ord_key(lo)));
-    hi = ord_val(__reduce_min_sync(mask, ord_key(hi)));
+    float a, b;
+    asm volatile("redux.sync.max.f32 %0, %1, %2;" : "=f"(a) : "f"(lo), "r"(mask));
+    asm volatile("redux.sync.min.f32 %0, %1, %2;" : "=f"(b) : "f"(hi), "r"(mask));
+    lo = a;
+    hi = b;
 }
 __device__ __forceinline__ void team_bounds(double &lo, double &hi, int S, int)
 {
@@ -587,9 +590,12 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
     const bool active = q_raw < p.chains;
     const long long q = active ? q_raw : (long long)p.chains - 1;  // idle teams shadow a real chain, write nothing
 
-    T *csm = reinterpret_cast<T *>(smem_raw) + (size_t)(wcta * TW + team) * (2 * sh.cpad + sh.mpad);
+    // per team in shared memory: c (cpad), w (cpad), r~ (mpad) and the uniforms of the
+    // current window of 4S moves
+    T *csm = reinterpret_cast<T *>(smem_raw) + (size_t)(wcta * TW + team) * (2 * sh.cpad + sh.mpad + 4 * S);
     T *wsm = csm + sh.cpad;
     T *rsm = wsm + sh.cpad;
+    T *usm = rsm + sh.mpad;
     T *Rq = p.R + (size_t)q * p.ldR;
     for (int m = sl; m < p.M; m += S) rsm[m] = Rq[m];
     T *Fq = p.F + (size_t)q * p.ldF;
@@ -600,13 +606,12 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
     T f[KV][VEC];
     unsigned long long n_deg = 0, n_zero = 0, n_bad = 0;
     int capped = 0;
-    unsigned long long rw0 = 0, rw1 = 0, rw2 = 0, rw3 = 0;
     const long long s_end = rg.sweep0 + rg.nsweeps;
     for (long long s = rg.sweep0; s < s_end && !failed; ++s) {
         // level of this sweep: same for every chain of the problem (Sec. IV.C)
         const int level = level_of_sweep(s, p.seed, p.problem_id, p.n_levels);
         const bool keep = s >= rg.burn_in;
-        long long win = -1;  // first move index covered by this lane's Philox words
+        long long win = -1;  // first move index of the window whose uniforms are in usm
         const int nb = p.level_nblocks[level];
         const BlockDesc *bd = p.blocks + p.level_first[level];
 
@@ -643,7 +648,9 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
             for (int j = 0; j < B.n; ++j) {
                 // what does not depend on the bounds first: c_j and the uniform
                 const T cj = j < B.np ? csm[j] : T(0);
-                // uniform of move t: word t%4 of Philox(ctr = {t/4, s, q, problem})
+                // uniform of move t: word t%4 of Philox(ctr = {t/4, s, q, problem}); the 4S
+                // uniforms of a window come from one Philox call per lane (lane sl: ctr
+                // win/4 + sl, moves win + 4 sl + 0..3)
                 const int t = B.start + j;
                 if (win < 0 || t >= win + 4 * S) {
                     win = (long long)(t / (4 * S)) * (4 * S);
@@ -651,13 +658,14 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     unsigned long long c1 = (unsigned long long)s, c2 = (unsigned long long)q + p.chain_offset,
                                        c3 = p.problem_id;
                     philox4x64_10(c0, c1, c2, c3, p.seed, 0ull);
-                    rw0 = c0; rw1 = c1; rw2 = c2; rw3 = c3;
+                    __syncwarp();   // the previous window is read by every lane
+                    usm[4 * sl] = uniform_from<T>(c0);
+                    usm[4 * sl + 1] = uniform_from<T>(c1);
+                    usm[4 * sl + 2] = uniform_from<T>(c2);
+                    usm[4 * sl + 3] = uniform_from<T>(c3);
+                    __syncwarp();
                 }
-                const int sel = t & 3;
-                const unsigned long long mine = sel == 0 ? rw0 : sel == 1 ? rw1 : sel == 2 ? rw2 : rw3;
-                const int src = (t >> 2) - (int)(win >> 2);
-                const unsigned long long word = __shfl_sync(0xffffffffu, mine, team_base + src);
-                const T u = uniform_from<T>(word);
+                const T u = usm[t - (int)win];
                 // this move's record
                 const bool ok = mbar_wait_ready(full + rp.slot, rp.phase, kWaitLimit);
                 if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
@@ -682,8 +690,8 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     delta = T(0);
                     ++n_bad;
                 }
-                if (j < B.np && sl == 0) wsm[j] = dj * delta;
                 fused_pass_smem<T, KV>(f, delta, st, st + B.rs, st + 2 * B.rs, kcnt, sl, S, lo, hi);
+                if (j < B.np && sl == 0) wsm[j] = dj * delta;
                 // release the record to the producer (one arrival per warp)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty + rp.slot);
