@@ -20,23 +20,23 @@ struct BlockDesc {
     int start;       // first grid point of the block
     int n;           // block width n_b
     int np;          // modes with a U column: min(M, n_b)
-    int rs;          // row stride of V/Rlo/Rhi rows (multiple of kRowAlign)
-    long long offV;  // V/Rlo/Rhi: n rows (Rlo/Rhi: n + 1 rows, the last all-NaN)
-    long long offR;  // Rlo/Rhi base
+    int rs;          // row stride of V/R rows (multiple of kRowAlign)
+    long long offV;  // V: n rows
+    long long offR;  // R = -1/V (NaN where V is left out): n + 1 rows, the last all-NaN
     long long offd;  // d, invd: n values
     long long offU;  // Ut: np x M (mode-major); Um: M x np (grid-major)
     long long offRec;  // move records of the block: n records of recstride elements
-    int recstride;     // elements per record (3 rs + 16 bytes, padded to 128 bytes)
+    int recstride;     // elements per record (2 rs + 16)
     int pad_;
 };
 
 // Device-side problem data in one precision T.
 template <class T>
 struct ProblemData {
-    const T *V, *Rlo, *Rhi;  // mode rows
+    const T *V, *R;          // mode rows V and R = -1/V (NaN where V is left out of the bounds)
     const T *d, *invd;       // singular values and their reciprocals (0 for zero modes)
     const T *meta;           // per mode, 16 bytes: {d, 1/d} (FP32: {d, 1/d, 0, 0})
-    const T *rec;            // per move j: {V_j, Rlo_{j+1}, Rhi_{j+1} (rs each), meta_j}
+    const T *rec;            // per move j: {V_j, R_{j+1} (rs each), d_j, 1/d_j}
     const T *Ut, *Um;        // U in two layouts
 };
 

@@ -293,7 +293,7 @@ struct WsLayout {
 
 // device buffers of one precision
 struct PrecBuffers {
-    void *V = nullptr, *Rlo = nullptr, *Rhi = nullptr, *d = nullptr, *invd = nullptr, *meta = nullptr,
+    void *V = nullptr, *R = nullptr, *d = nullptr, *invd = nullptr, *meta = nullptr,
          *rec = nullptr, *Ut = nullptr, *Um = nullptr;
 };
 
@@ -446,7 +446,7 @@ int upload(void **dst, const std::vector<T> &src)
 
 void free_prec(PrecBuffers &b)
 {
-    void *ptrs[] = {b.V, b.Rlo, b.Rhi, b.d, b.invd, b.meta, b.rec, b.Ut, b.Um};
+    void *ptrs[] = {b.V, b.R, b.d, b.invd, b.meta, b.rec, b.Ut, b.Um};
     for (void *x : ptrs)
         if (x) cudaFree(x);
     b = PrecBuffers{};
@@ -649,7 +649,7 @@ int build_precision(asm_problem *p, const HostFactors &hf, PrecBuffers &out)
     const int M = p->M;
     const T nan = std::numeric_limits<T>::quiet_NaN();
     constexpr int MW = 16 / sizeof(T);
-    std::vector<T> V(p->totV, T(0)), Rlo(p->totR, nan), Rhi(p->totR, nan), d(p->totd, T(0)),
+    std::vector<T> V(p->totV, T(0)), R(p->totR, nan), d(p->totd, T(0)),
         invd(p->totd, T(0)), meta((size_t)p->totd * MW, T(0)), rec(std::max<long long>(p->totRec, 1), T(0)),
         Ut(std::max<long long>(p->totU, 1), T(0)),
         Um(std::max<long long>(p->totU, 1), T(0));
@@ -663,9 +663,7 @@ int build_precision(asm_problem *p, const HostFactors &hf, PrecBuffers &out)
             for (int i = 0; i < B.n; ++i) {
                 V[B.offV + (size_t)j * B.rs + i] = (T)v[i];
                 if (std::fabs(v[i]) < 0x1p-40 * vmax) continue;   // left out of the bounds
-                const double r = -1.0 / v[i];
-                if (v[i] > 0.0) Rlo[B.offR + (size_t)j * B.rs + i] = (T)r;
-                else Rhi[B.offR + (size_t)j * B.rs + i] = (T)r;
+                R[B.offR + (size_t)j * B.rs + i] = (T)(-1.0 / v[i]);
             }
             d[B.offd + j] = (T)hd[j];
             invd[B.offd + j] = hd[j] > 0.0 ? (T)(1.0 / hd[j]) : T(0);
@@ -677,20 +675,19 @@ int build_precision(asm_problem *p, const HostFactors &hf, PrecBuffers &out)
                 Ut[B.offU + (size_t)j * M + m] = (T)hU[(size_t)j * M + m];
                 Um[B.offU + (size_t)m * B.np + j] = (T)hU[(size_t)j * M + m];
             }
-        // move records: {V_j, Rlo_{j+1}, Rhi_{j+1}, d_j, 1/d_j}
+        // move records: {V_j, R_{j+1}, d_j, 1/d_j}
         for (int j = 0; j < B.n; ++j) {
             T *r = &rec[B.offRec + (size_t)j * B.recstride];
             for (int i = 0; i < B.rs; ++i) {
                 r[i] = V[B.offV + (size_t)j * B.rs + i];
-                r[B.rs + i] = Rlo[B.offR + (size_t)(j + 1) * B.rs + i];
-                r[2 * B.rs + i] = Rhi[B.offR + (size_t)(j + 1) * B.rs + i];
+                r[B.rs + i] = R[B.offR + (size_t)(j + 1) * B.rs + i];
             }
-            r[3 * B.rs] = d[B.offd + j];
-            r[3 * B.rs + 1] = invd[B.offd + j];
+            r[2 * B.rs] = d[B.offd + j];
+            r[2 * B.rs + 1] = invd[B.offd + j];
         }
     }
     int rc;
-    if ((rc = upload(&out.V, V)) || (rc = upload(&out.Rlo, Rlo)) || (rc = upload(&out.Rhi, Rhi)) ||
+    if ((rc = upload(&out.V, V)) || (rc = upload(&out.R, R)) ||
         (rc = upload(&out.d, d)) || (rc = upload(&out.invd, invd)) || (rc = upload(&out.meta, meta)) || (rc = upload(&out.rec, rec)) ||
         (rc = upload(&out.Ut, Ut)) ||
         (rc = upload(&out.Um, Um)))
@@ -745,8 +742,7 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.level_nblocks = p->d_level_nblocks;
     sp.blocks = p->d_blocks;
     sp.pd.V = (const T *)b.V;
-    sp.pd.Rlo = (const T *)b.Rlo;
-    sp.pd.Rhi = (const T *)b.Rhi;
+    sp.pd.R = (const T *)b.R;
     sp.pd.d = (const T *)b.d;
     sp.pd.invd = (const T *)b.invd;
     sp.pd.Ut = (const T *)b.Ut;
@@ -1223,7 +1219,7 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
             B.offR = oR; oR += (long long)(B.n + 1) * B.rs;
             B.offd = od; od += B.n;
             B.offU = oU; oU += (long long)B.np * M;
-            B.recstride = 3 * B.rs + 16;   // elements; 16 holds the mode data in both precisions
+            B.recstride = 2 * B.rs + 16;   // elements; 16 holds the mode data in both precisions
             B.offRec = oRec; oRec += (long long)B.n * B.recstride;
             p->max_rec = std::max(p->max_rec, B.recstride);
             p->blocks.push_back(B);

@@ -5,14 +5,15 @@
 // runs 32/S chains.  While a block is visited, the team keeps the block's part
 // of the chain state f in registers: lane s holds the 16-byte vectors
 // k*S + s (k < KV) of the block.  Mode rows (V, and the masked reciprocals
-// Rlo/Rhi that give the bounds of Eq. modeLimits) are read as 16-byte vectors
-// through the read-only cache; every chain of the same problem reads the same
-// rows at the same time.  The tracked residual r~ = g~ - K~ f and the block's
+// R = -1/V that give the bounds of Eq. modeLimits) are read as 16-byte vectors
+// from a CTA-shared ring of move records; every chain of the same problem reads
+// the same rows at the same time.  The tracked residual r~ = g~ - K~ f and the block's
 // projections c_j = U_j^T r~ live in shared memory.
 //
 // One move of mode j (Sec. IV.B, "sample e_i' from a univariate Gaussian ...
 // truncated to the interval for which f' >= 0"):
-//   [lo, hi]  = interval of delta from the previous pass (team max/min reduce)
+//   [lo, hi]  = interval of delta from the previous pass (team minima of the
+//               bound keys, see BoundKey)
 //   delta     ~ N(c_j/d_j, 1/d_j^2) on [lo, hi] by the inverse CDF (flat if d_j = 0)
 //   pass      f += delta V_j, clamp at 0, and the bounds of mode j+1 in the same
 //             sweep over the registers
@@ -256,53 +257,68 @@ __device__ __forceinline__ void ldv(const double *p, double (&o)[2])
     o[0] = v.x; o[1] = v.y;
 }
 
-// f += delta * V (clamped at 0), then the bounds of the next mode from the
-// updated f: lo = max over V>0 of -f/V, hi = min over V<0 of -f/V.  Rlo/Rhi
-// hold -1/V where V has the right sign and NaN elsewhere; fmax/fmin drop NaN.
+// Bound keys.  With x >= +0 and R = -1/V (NaN where V is left out of the
+// bounds), t = x R is <= -0 exactly when V > 0 (a lower-bound candidate for
+// the step) and >= +0 when V < 0 (an upper-bound candidate).  Read as integers
+// of the same width, the largest lower candidate is the SIGNED minimum of the
+// bit patterns of all t (negative floats order by magnitude, above every
+// negative the -inf of the initial key) and the smallest upper candidate the
+// UNSIGNED minimum (negative floats and NaN lie above +inf).  One multiply and
+// two integer minima per element, one R row instead of two.
+template <class T> struct BoundKey;
+template <> struct BoundKey<float> {
+    using S = int;
+    using U = unsigned;
+    static constexpr S lo0 = (S)0xff800000;   // -inf
+    static constexpr U hi0 = 0x7f800000u;     // +inf
+    static __device__ __forceinline__ S bits(float x) { return __float_as_int(x); }
+    static __device__ __forceinline__ float lo_of(S k) { return __int_as_float(k); }
+    static __device__ __forceinline__ float hi_of(U k) { return __uint_as_float(k); }
+};
+template <> struct BoundKey<double> {
+    using S = long long;
+    using U = unsigned long long;
+    static constexpr S lo0 = (S)0xfff0000000000000ull;
+    static constexpr U hi0 = 0x7ff0000000000000ull;
+    static __device__ __forceinline__ S bits(double x) { return __double_as_longlong(x); }
+    static __device__ __forceinline__ double lo_of(S k) { return __longlong_as_double(k); }
+    static __device__ __forceinline__ double hi_of(U k) { return __longlong_as_double((long long)k); }
+};
+template <class T>
+__device__ __forceinline__ void key_update(typename BoundKey<T>::S &lk, typename BoundKey<T>::U &hk, T t)
+{
+    const typename BoundKey<T>::S k = BoundKey<T>::bits(t);
+    lk = k < lk ? k : lk;
+    const typename BoundKey<T>::U ku = (typename BoundKey<T>::U)k;
+    hk = ku < hk ? ku : hk;
+}
+
+// f += delta * V (clamped at +0), then the lane's bound keys of the next mode
+// from the updated f and that mode's R row (rows read from global memory).
 template <class T, int KV>
-__device__ __forceinline__ void fused_pass(T (&f)[KV][VecOf<T>::n], T delta,
-                                           const T *__restrict__ vrow, const T *__restrict__ rlrow,
-                                           const T *__restrict__ rhrow, int kcnt, int sl, int S,
-                                           T &lo, T &hi)
+__device__ __forceinline__ void fused_pass(T (&f)[KV][VecOf<T>::n], T delta, const T *__restrict__ vrow,
+                                           const T *__restrict__ rrow, int kcnt, int sl, int S,
+                                           typename BoundKey<T>::S &lk, typename BoundKey<T>::U &hk)
 {
     constexpr int VEC = VecOf<T>::n;
-    T la[VEC], ha[VEC];
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) {
-        la[v] = -CUDART_INF_F;
-        ha[v] = CUDART_INF_F;
-    }
+    lk = BoundKey<T>::lo0;
+    hk = BoundKey<T>::hi0;
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
         if (k < kcnt) {
             const int idx = VEC * (k * S + sl);
-            T vv[VEC], rl[VEC], rh[VEC];
+            T vv[VEC], rr[VEC];
             ldv(vrow + idx, vv);
-            ldv(rlrow + idx, rl);
-            ldv(rhrow + idx, rh);
+            ldv(rrow + idx, rr);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 T x = m_fma(delta, vv[v], f[k][v]);
                 x = m_max(x, T(0));
                 f[k][v] = x;
-                la[v] = m_max(la[v], x * rl[v]);
-                ha[v] = m_min(ha[v], x * rh[v]);
+                key_update<T>(lk, hk, x * rr[v]);
             }
         }
     }
-    lo = la[0];
-    hi = ha[0];
-#pragma unroll
-    for (int v = 1; v < VEC; ++v) {
-        lo = m_max(lo, la[v]);
-        hi = m_min(hi, ha[v]);
-    }
-}
-
-template <class T>
-__device__ __forceinline__ T shfl_xor(T v, int off)
-{
-    return __shfl_xor_sync(0xffffffffu, v, off);
 }
 
 // --------------------------------------------------------------------------
@@ -377,23 +393,24 @@ __device__ __forceinline__ void fence_mbar_init()
 
 constexpr int kWaitLimit = 1 << 22;
 
-// Team-wide max of lo and min of hi.  FP32: one floating-point redux
-// instruction each (neither value is ever NaN).  FP64: a butterfly of shuffles.
-__device__ __forceinline__ void team_bounds(float &lo, float &hi, int S, int team_base)
+// Team-wide bounds from the lanes' keys: signed and unsigned integer minima
+// (FP32: one redux instruction each; FP64: a butterfly of shuffles).
+__device__ __forceinline__ void team_bounds(int lk, unsigned hk, float &lo, float &hi, int S, int team_base)
 {
     const unsigned mask = S == 32 ? 0xffffffffu : (((1u << S) - 1u) << team_base);
-    float a, b;
-    asm volatile("redux.sync.max.f32 %0, %1, %2;" : "=f"(a) : "f"(lo), "r"(mask));
-    asm volatile("redux.sync.min.f32 %0, %1, %2;" : "=f"(b) : "f"(hi), "r"(mask));
-    lo = a;
-    hi = b;
+    lo = __int_as_float(__reduce_min_sync(mask, lk));
+    hi = __uint_as_float(__reduce_min_sync(mask, hk));
 }
-__device__ __forceinline__ void team_bounds(double &lo, double &hi, int S, int)
+__device__ __forceinline__ void team_bounds(long long lk, unsigned long long hk, double &lo, double &hi, int S, int)
 {
     for (int off = 1; off < S; off <<= 1) {
-        lo = fmax(lo, __shfl_xor_sync(0xffffffffu, lo, off));
-        hi = fmin(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+        const long long l2 = __shfl_xor_sync(0xffffffffu, lk, off);
+        const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hk, off);
+        lk = l2 < lk ? l2 : lk;
+        hk = h2 < hk ? h2 : hk;
     }
+    lo = __longlong_as_double(lk);
+    hi = __longlong_as_double((long long)hk);
 }
 
 // 16-byte vector loads from shared memory
@@ -408,44 +425,31 @@ __device__ __forceinline__ void lds_v(const double *p, double (&o)[2])
     o[0] = v.x; o[1] = v.y;
 }
 
-// f += delta * V (clamped at 0) and the bounds of the next mode, rows read
-// from a shared-memory stage.
+// f += delta * V (clamped at +0) and the lane's bound keys of the next mode,
+// rows read from a shared-memory stage.
 template <class T, int KV>
-__device__ __forceinline__ void fused_pass_smem(T (&f)[KV][VecOf<T>::n], T delta, const T *vrow,
-                                                const T *rlrow, const T *rhrow, int kcnt, int sl, int S,
-                                                T &lo, T &hi)
+__device__ __forceinline__ void fused_pass_smem(T (&f)[KV][VecOf<T>::n], T delta, const T *vrow, const T *rrow,
+                                                int kcnt, int sl, int S, typename BoundKey<T>::S &lk,
+                                                typename BoundKey<T>::U &hk)
 {
     constexpr int VEC = VecOf<T>::n;
-    T la[VEC], ha[VEC];
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) {
-        la[v] = -CUDART_INF_F;
-        ha[v] = CUDART_INF_F;
-    }
+    lk = BoundKey<T>::lo0;
+    hk = BoundKey<T>::hi0;
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
         if (k < kcnt) {
             const int idx = VEC * (k * S + sl);
-            T vv[VEC], rl[VEC], rh[VEC];
+            T vv[VEC], rr[VEC];
             lds_v(vrow + idx, vv);
-            lds_v(rlrow + idx, rl);
-            lds_v(rhrow + idx, rh);
+            lds_v(rrow + idx, rr);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 T x = m_fma(delta, vv[v], f[k][v]);
                 x = m_max(x, T(0));
                 f[k][v] = x;
-                la[v] = m_max(la[v], x * rl[v]);
-                ha[v] = m_min(ha[v], x * rh[v]);
+                key_update<T>(lk, hk, x * rr[v]);
             }
         }
-    }
-    lo = la[0];
-    hi = ha[0];
-#pragma unroll
-    for (int v = 1; v < VEC; ++v) {
-        lo = m_max(lo, la[v]);
-        hi = m_min(hi, ha[v]);
     }
 }
 
@@ -626,25 +630,28 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     const int nl = VEC * (k * S + sl) + v;
                     f[k][v] = (k < kcnt && nl < B.n) ? Fq[B.start + nl] : T(0);
                 }
-            // c = U_b^T r~ (lanes split the modes; four partial sums per mode)
+            // c = U_b^T r~ (lanes split the modes; eight loads in flight, eight partial sums)
             const T *Um = p.pd.Um + B.offU;
             for (int j = sl; j < B.np; j += S) {
-                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+                T a[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a[i] = T(0);
                 int m = 0;
-                for (; m + 3 < p.M; m += 4) {
-                    a0 = m_fma(__ldg(Um + (size_t)m * B.np + j), rsm[m], a0);
-                    a1 = m_fma(__ldg(Um + (size_t)(m + 1) * B.np + j), rsm[m + 1], a1);
-                    a2 = m_fma(__ldg(Um + (size_t)(m + 2) * B.np + j), rsm[m + 2], a2);
-                    a3 = m_fma(__ldg(Um + (size_t)(m + 3) * B.np + j), rsm[m + 3], a3);
+                for (; m + 7 < p.M; m += 8) {
+                    T x[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) x[i] = __ldg(Um + (size_t)(m + i) * B.np + j);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) a[i] = m_fma(x[i], rsm[m + i], a[i]);
                 }
-                for (; m < p.M; ++m) a0 = m_fma(__ldg(Um + (size_t)m * B.np + j), rsm[m], a0);
-                csm[j] = (a0 + a1) + (a2 + a3);
+                for (; m < p.M; ++m) a[0] = m_fma(__ldg(Um + (size_t)m * B.np + j), rsm[m], a[0]);
+                csm[j] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
             }
             __syncwarp();
 
-            T lo, hi;
-            fused_pass<T, KV>(f, T(0), p.pd.V + B.offV, p.pd.Rlo + B.offR, p.pd.Rhi + B.offR, kcnt, sl, S,
-                              lo, hi);  // bounds of mode 0
+            typename BoundKey<T>::S lk;
+            typename BoundKey<T>::U hk;
+            fused_pass<T, KV>(f, T(0), p.pd.V + B.offV, p.pd.R + B.offR, kcnt, sl, S, lk, hk);  // keys of mode 0
             for (int j = 0; j < B.n; ++j) {
                 // what does not depend on the bounds first: c_j and the uniform
                 const T cj = j < B.np ? csm[j] : T(0);
@@ -673,9 +680,10 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     break;
                 }
                 const T *st = reinterpret_cast<const T *>(stages + (size_t)rp.slot * sh.stage_bytes);
-                const T dj = st[3 * B.rs], ij = st[3 * B.rs + 1];
+                const T dj = st[2 * B.rs], ij = st[2 * B.rs + 1];
 
-                team_bounds(lo, hi, S, team_base);
+                T lo, hi;
+                team_bounds(lk, hk, lo, hi, S, team_base);
                 T delta;
                 if (!(hi > lo)) {
                     delta = T(0);
@@ -690,7 +698,7 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     delta = T(0);
                     ++n_bad;
                 }
-                fused_pass_smem<T, KV>(f, delta, st, st + B.rs, st + 2 * B.rs, kcnt, sl, S, lo, hi);
+                fused_pass_smem<T, KV>(f, delta, st, st + B.rs, kcnt, sl, S, lk, hk);
                 if (j < B.np && sl == 0) wsm[j] = dj * delta;
                 // release the record to the producer (one arrival per warp)
                 __syncwarp();
@@ -699,19 +707,22 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
             }
             if (failed) break;
             __syncwarp();
-            // exit: r~ -= U_b w (lanes split the data points; four partial sums)
+            // exit: r~ -= U_b w (lanes split the data points; eight loads in flight, eight partial sums)
             const T *Ut = p.pd.Ut + B.offU;
             for (int m = sl; m < p.M; m += S) {
-                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+                T a[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a[i] = T(0);
                 int j = 0;
-                for (; j + 3 < B.np; j += 4) {
-                    a0 = m_fma(__ldg(Ut + (size_t)j * p.M + m), wsm[j], a0);
-                    a1 = m_fma(__ldg(Ut + (size_t)(j + 1) * p.M + m), wsm[j + 1], a1);
-                    a2 = m_fma(__ldg(Ut + (size_t)(j + 2) * p.M + m), wsm[j + 2], a2);
-                    a3 = m_fma(__ldg(Ut + (size_t)(j + 3) * p.M + m), wsm[j + 3], a3);
+                for (; j + 7 < B.np; j += 8) {
+                    T x[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) x[i] = __ldg(Ut + (size_t)(j + i) * p.M + m);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) a[i] = m_fma(x[i], wsm[j + i], a[i]);
                 }
-                for (; j < B.np; ++j) a0 = m_fma(__ldg(Ut + (size_t)j * p.M + m), wsm[j], a0);
-                rsm[m] -= (a0 + a1) + (a2 + a3);
+                for (; j < B.np; ++j) a[0] = m_fma(__ldg(Ut + (size_t)j * p.M + m), wsm[j], a[0]);
+                rsm[m] -= ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
             }
             // write the block back and accumulate the kept sweep
 #pragma unroll
