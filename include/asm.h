@@ -141,7 +141,7 @@ int asm_problem_count(const asm_problem *p);
 
 /* Autotuner of the sweep launch (no counterpart in the paper).  Times every
  * candidate shape -- lanes per chain S in {32, 16, 8} times chain warps per
- * CTA in {heuristic, 2, 4, 6, 7, 8}, where it fits -- on one warm-up and three
+ * CTA in {heuristic, 2, 3, 4, 5, 6, 7}, where it fits -- on one warm-up and three
  * timed sweeps of fresh trial chains in the caller's workspace (same layout
  * and size rule as asm_sample), and keeps the fastest for later asm_sample
  * calls on p.  The shape changes no result: every chain does the same

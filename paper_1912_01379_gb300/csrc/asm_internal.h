@@ -125,6 +125,10 @@ cudaError_t launch_split_k(const double *KtT, int M, int N, int ldK, float *Khi,
 int sweep_ctas_per_sm_f32(const LaunchShape &shape, int kv, bool batch);
 int sweep_ctas_per_sm_f64(const LaunchShape &shape, int kv, bool batch);
 // Largest supported kv per precision.
+// Consumer warps per CTA: at most 7, so that a CTA (consumers + the producer)
+// has at most 8 warps, two per SM sub-partition, and a thread may hold up to
+// 255 registers (9 warps would put three on one sub-partition: 168).
+constexpr int kMaxConsumers = 7;
 constexpr int kMaxKvF32 = 16;   // 64 floats per lane
 constexpr int kMaxKvF64 = 32;   // 64 doubles per lane
 

@@ -796,10 +796,11 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
     sh.mpad = round_up_int(std::max(max_M, 1), 32);
     int consumers = want_consumers > 0
                         ? want_consumers
-                        : (int)std::min<long long>(8, std::max<long long>(1, (total_warps + kSMs - 1) / kSMs));
+                        : (int)std::min<long long>(kMaxConsumers,
+                                                   std::max<long long>(1, (total_warps + kSMs - 1) / kSMs));
     if (const char *e = std::getenv("ASM_CONSUMERS_PER_CTA")) {   // tuning override
         const int c = std::atoi(e);
-        if (c >= 1 && c <= 8) consumers = c;
+        if (c >= 1 && c <= kMaxConsumers) consumers = c;
     }
     sh.stage_bytes = (int)align_up((size_t)max_rec * sizeof(T), 128);
     auto fixed = [&](int c) {
@@ -1491,7 +1492,7 @@ int asm_tune(asm_problem *p, int chains, int precision, void *d_workspace, size_
     float best = 0.f;
     bool any = false;
     const int teams[] = {32, 16, 8};
-    const int conss[] = {0, 2, 4, 6, 7, 8};   // 0: the built-in heuristic
+    const int conss[] = {0, 2, 3, 4, 5, 6, 7};   // 0: the built-in heuristic
     for (int S : teams) {
         for (int c : conss) {
             p->team = S;

@@ -427,8 +427,10 @@ __device__ __forceinline__ void lds_v(const double *p, double (&o)[2])
 
 // f += delta * V (clamped at +0) and the lane's bound keys of the next mode,
 // rows read from a shared-memory stage.
+// The caller loads chunk 0 (v0, r0) ahead of the draw; kcnt >= 1.
 template <class T, int KV>
-__device__ __forceinline__ void fused_pass_smem(T (&f)[KV][VecOf<T>::n], T delta, const T *vrow, const T *rrow,
+__device__ __forceinline__ void fused_pass_smem(T (&f)[KV][VecOf<T>::n], T delta, const T (&v0)[VecOf<T>::n],
+                                                const T (&r0)[VecOf<T>::n], const T *vrow, const T *rrow,
                                                 int kcnt, int sl, int S, typename BoundKey<T>::S &lk,
                                                 typename BoundKey<T>::U &hk)
 {
@@ -440,8 +442,16 @@ __device__ __forceinline__ void fused_pass_smem(T (&f)[KV][VecOf<T>::n], T delta
         if (k < kcnt) {
             const int idx = VEC * (k * S + sl);
             T vv[VEC], rr[VEC];
-            lds_v(vrow + idx, vv);
-            lds_v(rrow + idx, rr);
+            if (k == 0) {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    vv[v] = v0[v];
+                    rr[v] = r0[v];
+                }
+            } else {
+                lds_v(vrow + idx, vv);
+                lds_v(rrow + idx, rr);
+            }
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 T x = m_fma(delta, vv[v], f[k][v]);
@@ -527,6 +537,16 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
+// Arrival by lane 0 of the warp only, as a predicated instruction (no branch).
+__device__ __forceinline__ void mbar_arrive_lane0(unsigned long long *bar, int lane)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.eq.s32 p, %1, 0;\n\t"
+        "@p mbarrier.arrive.shared::cta.b64 _, [%0];\n\t}" ::"r"(smem_addr(bar)),
+        "r"(lane)
+        : "memory");
+}
 
 // --------------------------------------------------------------------------
 // The producer warp: one bulk copy per move of the item into the ring, after
@@ -608,7 +628,7 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
     __syncwarp();
 
     T f[KV][VEC];
-    unsigned long long n_deg = 0, n_zero = 0, n_bad = 0;
+    unsigned n_deg = 0, n_zero = 0, n_bad = 0;   // per launch: at most 64 sweeps of moves
     int capped = 0;
     const long long s_end = rg.sweep0 + rg.nsweeps;
     for (long long s = rg.sweep0; s < s_end && !failed; ++s) {
@@ -681,6 +701,9 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                 }
                 const T *st = reinterpret_cast<const T *>(stages + (size_t)rp.slot * sh.stage_bytes);
                 const T dj = st[2 * B.rs], ij = st[2 * B.rs + 1];
+                T v0[VEC], r0[VEC];   // chunk 0 of the pass: independent of the draw, loaded first
+                lds_v(st + VEC * sl, v0);
+                lds_v(st + B.rs + VEC * sl, r0);
 
                 T lo, hi;
                 team_bounds(lk, hk, lo, hi, S, team_base);
@@ -698,11 +721,11 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     delta = T(0);
                     ++n_bad;
                 }
-                fused_pass_smem<T, KV>(f, delta, st, st + B.rs, kcnt, sl, S, lk, hk);
+                fused_pass_smem<T, KV>(f, delta, v0, r0, st, st + B.rs, kcnt, sl, S, lk, hk);
                 if (j < B.np && sl == 0) wsm[j] = dj * delta;
                 // release the record to the producer (one arrival per warp)
                 __syncwarp();
-                if (lane == 0) mbar_arrive(empty + rp.slot);
+                mbar_arrive_lane0(empty + rp.slot, lane);
                 ring_next(rp, D);
             }
             if (failed) break;
@@ -750,9 +773,9 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
     if (active) {
         for (int m = sl; m < p.M; m += S) Rq[m] = rsm[m];
         if (sl == 0) {
-            if (n_deg) atomicAdd(&p.counters->degenerate, n_deg);
-            if (n_zero) atomicAdd(&p.counters->zero_mode, n_zero);
-            if (n_bad) atomicAdd(&p.counters->nonfinite, n_bad);
+            if (n_deg) atomicAdd(&p.counters->degenerate, (unsigned long long)n_deg);
+            if (n_zero) atomicAdd(&p.counters->zero_mode, (unsigned long long)n_zero);
+            if (n_bad) atomicAdd(&p.counters->nonfinite, (unsigned long long)n_bad);
             if (capped) atomicAdd(&p.counters->tail_capped, (unsigned long long)capped);
         }
     }
@@ -767,7 +790,7 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
 // into shared memory.
 // --------------------------------------------------------------------------
 template <class T, int KV, bool BATCH>
-__global__ void __launch_bounds__(288) sweep_kernel(const __grid_constant__ SweepParams<T> p0,
+__global__ void __launch_bounds__(32 * (kMaxConsumers + 1), 1) sweep_kernel(const __grid_constant__ SweepParams<T> p0,
                                                     const SweepParams<T> *__restrict__ probs,
                                                     const WorkItem *__restrict__ items, RunCtrl *ctrl,
                                                     const __grid_constant__ LaunchShape shape)
