@@ -220,12 +220,13 @@ def batch_side(args, asm, torch, stream):
            "chains_per_problem": chains, "sweeps": args.batch_sweeps}
     for prec, key, sweeps in ((asm.ASM_MIXED, "mixed", args.batch_sweeps),
                               (asm.ASM_FP64, "fp64", max(64, args.batch_sweeps // 4))):
-        team, cons = b.tune(chains, precision=prec)
+        b.tune(chains, precision=prec)
         b.sample(chains, 0, 1, 11, precision=prec)   # warm-up launch
         t = _timed(torch, stream, lambda: b.sample(chains, 0, sweeps, 12, precision=prec))
         st = b.status()
         out[key] = {"updates_per_s": chains * sweeps * sumN / t, "seconds": t, "sweeps": sweeps,
                     "team_lanes": st["team_lanes"], "consumers_per_cta": st["consumers_per_cta"],
+                    "ctas_per_sm_budget": st["min_blocks"],
                     "ctas": st["ctas"], "work_items": st["work_items"], "graph_replays": st["graph_replays"],
                     "timeouts": st["timeouts"]}
     out["speedup_mixed_vs_fp64"] = out["mixed"]["updates_per_s"] / out["fp64"]["updates_per_s"]
@@ -235,7 +236,8 @@ def batch_side(args, asm, torch, stream):
 def grid_side(args, asm, torch, stream):
     """Grid-size sweep (N_tau = 400, beta = 50, 16 blocks, 8192 chains) at
     N_omega in {250, 500, 1000, 2000}: mixed path (tensor-core refresh) and
-    plain FP64 path rates over one refresh period."""
+    plain FP64 path rates over one refresh period, each with the launch shape
+    asm_tune picks."""
     rows = []
     for N in (250, 500, 1000, 2000):
         p = W.grid_sweep_problem(N, "uniform")
@@ -244,11 +246,14 @@ def grid_side(args, asm, torch, stream):
         row = {"N_omega": N, "N_tau": p.M, "chains": chains}
         for prec, key, sweeps in ((asm.ASM_MIXED, "mixed", args.grid_sweeps),
                                   (asm.ASM_FP64, "fp64", max(2, args.grid_sweeps // 8))):
+            gp.tune(chains, precision=prec)
             gp.sample(chains, 0, 1, 21, precision=prec)
             t = _timed(torch, stream, lambda: gp.sample(chains, 0, sweeps, 22, precision=prec))
             st = gp.status()
             row[key] = {"updates_per_s": chains * sweeps * N / t, "sweeps": sweeps,
-                        "tc_refreshes": st["tc_refreshes"], "timeouts": st["timeouts"]}
+                        "tc_refreshes": st["tc_refreshes"], "timeouts": st["timeouts"],
+                        "shape": {"team_lanes": st["team_lanes"], "consumers_per_cta": st["consumers_per_cta"],
+                                  "ctas_per_sm_budget": st["min_blocks"]}}
         row["speedup_mixed_vs_fp64"] = row["mixed"]["updates_per_s"] / row["fp64"]["updates_per_s"]
         rows.append(row)
         del gp

@@ -116,6 +116,8 @@ typedef struct {
     int32_t consumers_per_cta;  /* chain warps per CTA of the last sweep launch */
     int32_t ctas;               /* CTAs of the last sweep launch (persistent) */
     int32_t work_items;         /* (problem, chain group) items of the last sweep launch */
+    int32_t min_blocks;         /* CTAs per SM the last sweep launch's registers were budgeted for (1, 2) */
+    int32_t reserved_;
 } asm_stats;
 
 /* Set-up (Sec. IV: whitening C^{-1} = T^T T by Cholesky, K~ = T K, g~ = T G;
@@ -141,17 +143,19 @@ int asm_problem_count(const asm_problem *p);
 
 /* Autotuner of the sweep launch (no counterpart in the paper).  Times every
  * candidate shape -- lanes per chain S in {32, 16, 8} times chain warps per
- * CTA in {heuristic, 2, 3, 4, 5, 6, 7}, where it fits -- on one warm-up and three
+ * CTA in {heuristic, 2, 3, 4, 5, 6, 7} times the register budget (kernels
+ * compiled for one CTA per SM, up to 255 registers per thread, or for two,
+ * 128), where it fits -- on one warm-up and three
  * timed sweeps of fresh trial chains in the caller's workspace (same layout
  * and size rule as asm_sample), and keeps the fastest for later asm_sample
  * calls on p.  The shape changes no result: every chain does the same
  * arithmetic in the same order under every shape.  The workspace's contents
  * are overwritten, so the next asm_sample must start fresh chains
  * (ASM_SAMPLE_CONTINUE then fails with ASM_ERR_STATE).  Synchronises
- * `stream`.  team_out / consumers_out (may be NULL) receive the choice
- * (consumers 0 = the built-in heuristic). */
+ * `stream`.  team_out / consumers_out / min_blocks_out (may be NULL) receive
+ * the choice (consumers 0 = the built-in heuristic; min_blocks 1 or 2). */
 int asm_tune(asm_problem *p, int chains, int precision, void *d_workspace, size_t workspace_bytes,
-             void *stream, int *team_out, int *consumers_out);
+             void *stream, int *team_out, int *consumers_out, int *min_blocks_out);
 
 /* Bytes of device workspace asm_sample needs for `chains` chains (per problem)
  * at `precision` (ASM_FP64 or ASM_MIXED); 0 for invalid arguments. */

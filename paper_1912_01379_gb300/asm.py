@@ -44,7 +44,8 @@ class asm_stats(ct.Structure):
                 ("timed_launches", ct.c_int64), ("sweep_kernel_ms", ct.c_double),
                 ("timeouts", ct.c_int64), ("graph_replays", ct.c_int64), ("tc_refreshes", ct.c_int64),
                 ("team_lanes", ct.c_int32),
-                ("consumers_per_cta", ct.c_int32), ("ctas", ct.c_int32), ("work_items", ct.c_int32)]
+                ("consumers_per_cta", ct.c_int32), ("ctas", ct.c_int32), ("work_items", ct.c_int32),
+                ("min_blocks", ct.c_int32), ("reserved_", ct.c_int32)]
 
 
 EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",
@@ -106,7 +107,7 @@ def load(build_if_missing: bool = True):
     L.asm_average_at.argtypes = [ct.c_void_p, ct.c_int, _dp, _dp, _dp, _dp]
     L.asm_average_at.restype = ct.c_int
     L.asm_tune.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_size_t, ct.c_void_p,
-                           ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
+                           ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
     L.asm_tune.restype = ct.c_int
     _lib = L
     return L
@@ -208,13 +209,15 @@ class _Handle:
 
     def tune(self, chains, precision=ASM_MIXED, stream=None, workspace=None):
         """asm_tune: picks the fastest launch shape (lanes per chain, chain warps
-        per CTA) for `chains` chains; returns (team_lanes, consumers)."""
+        per CTA, register budget) for `chains` chains; returns
+        (team_lanes, consumers, min_blocks)."""
         torch, workspace = self._workspace(chains, precision, workspace)
         s = stream if stream is not None else torch.cuda.current_stream()
-        team, cons = ct.c_int(0), ct.c_int(0)
+        team, cons, mb = ct.c_int(0), ct.c_int(0), ct.c_int(0)
         _check(load().asm_tune(self._h, chains, precision, ct.c_void_p(workspace.data_ptr()), workspace.numel(),
-                               ct.c_void_p(s.cuda_stream), ct.byref(team), ct.byref(cons)), "asm_tune")
-        return team.value, cons.value
+                               ct.c_void_p(s.cuda_stream), ct.byref(team), ct.byref(cons), ct.byref(mb)),
+               "asm_tune")
+        return team.value, cons.value, mb.value
 
     def set_stream_ids(self, problem_id=0, chain_offset=0):
         _check(load().asm_set_stream_ids(self._h, ct.c_uint64(problem_id), ct.c_uint64(chain_offset)),

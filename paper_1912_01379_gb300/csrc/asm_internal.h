@@ -86,6 +86,7 @@ struct LaunchShape {
     int cpad;                         // shared-memory stride of the c/w buffers (>= max np)
     int mpad;                         // shared-memory stride of the residual (>= max M)
     int n_items;                      // (problem, chain group) work items
+    int minb;                         // register budget: 1 or 2 CTAs per SM
 };
 
 // Per-launch control block in device memory: the work queue and the launch's
@@ -103,16 +104,22 @@ struct WorkItem {
     int problem, group;
 };
 
-// Launchers (asm_sweep_f32.cu / asm_sweep_f64.cu).  kv: 16-byte vectors per lane.
+// Launchers (asm_sweep_{f32,f64}{,_m2}.cu).  kv: 16-byte vectors per lane.
 // Persistent: `ctas` CTAs of (consumers + 1) warps pull work items from
 // ctrl->queue (reset to 0 before the launch).  One problem (batch = false):
 // its parameters p0 travel by value in the launch; several (batch = true):
-// work item problems index the device array probs.
-cudaError_t launch_sweeps_f32(const SweepParams<float> &p0, const SweepParams<float> *probs, const WorkItem *items,
-                              RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch, int ctas, cudaStream_t s);
-cudaError_t launch_sweeps_f64(const SweepParams<double> &p0, const SweepParams<double> *probs,
-                              const WorkItem *items, RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch,
-                              int ctas, cudaStream_t s);
+// work item problems index the device array probs.  _m1 kernels budget the
+// registers for one CTA per SM (up to 255 per thread), _m2 for two (128).
+#define ASM_DECLARE_SWEEP_LAUNCHER(T, NAME)                                                                   \
+    cudaError_t launch_sweeps_##NAME(const SweepParams<T> &p0, const SweepParams<T> *probs, const WorkItem *items, \
+                                     RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch, int ctas,     \
+                                     cudaStream_t s);                                                          \
+    int sweep_ctas_per_sm_##NAME(const LaunchShape &shape, int kv, bool batch);
+ASM_DECLARE_SWEEP_LAUNCHER(float, f32_m1)
+ASM_DECLARE_SWEEP_LAUNCHER(float, f32_m2)
+ASM_DECLARE_SWEEP_LAUNCHER(double, f64_m1)
+ASM_DECLARE_SWEEP_LAUNCHER(double, f64_m2)
+#undef ASM_DECLARE_SWEEP_LAUNCHER
 // Tensor-core residual refresh of the mixed path (asm_refresh_tc.cu): grid of
 // (chain tiles of 128) x n_problems CTAs; max_bn = the largest refresh_tc_bn(M).
 cudaError_t launch_refresh_tc(const SweepParams<float> *probs, int n_problems, int chains, int max_bn, bool track_drift,

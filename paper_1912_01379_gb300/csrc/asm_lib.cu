@@ -338,25 +338,26 @@ struct asm_problem {
     bool have_run = false;
     // launch shape chosen by asm_tune (0: the built-in heuristic)
     int tuned_consumers = 0;
+    int tuned_minb = 0;   // CTAs per SM the registers are budgeted for (0: heuristic)
     // one refresh period (advance the range, sweep, refresh) as a CUDA graph
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     struct GraphKey {
         const void *ws_all = nullptr;
-        int chains = 0, precision = -1, kv = 0, ctas = 0, S = 0, consumers = 0, depth = 0, n_items = 0;
+        int chains = 0, precision = -1, kv = 0, ctas = 0, S = 0, consumers = 0, depth = 0, n_items = 0, minb = 0;
         size_t refresh_smem = 0;
         unsigned long long seed = 0, problem_id = 0, chain_offset = 0;
         bool operator==(const GraphKey &o) const
         {
             return ws_all == o.ws_all && chains == o.chains && precision == o.precision && kv == o.kv &&
                    ctas == o.ctas && S == o.S && consumers == o.consumers && depth == o.depth &&
-                   n_items == o.n_items && refresh_smem == o.refresh_smem && seed == o.seed &&
+                   n_items == o.n_items && minb == o.minb && refresh_smem == o.refresh_smem && seed == o.seed &&
                    problem_id == o.problem_id && chain_offset == o.chain_offset;
         }
     } gkey;
     long long graph_replays = 0, tc_refreshes = 0;
     bool refresh_fp64 = false;   // mixed path: FP64 CUDA-core refresh instead of the tensor cores
-    int last_team = 0, last_consumers = 0, last_ctas = 0, last_items = 0;   // shape of the last sweep launch
+    int last_team = 0, last_consumers = 0, last_ctas = 0, last_items = 0, last_minb = 0;   // last sweep launch
     bool no_graph = false;    // direct launches only (the allocation-free entry point)
     // launch bookkeeping
     long long sweep_launches = 0, other_launches = 0, timed_launches = 0;
@@ -781,13 +782,16 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
 // shape covers the largest problem.
 int ctas_per_sm(int precision, const LaunchShape &sh, int kv, bool batch)
 {
-    return precision == ASM_FP64 ? sweep_ctas_per_sm_f64(sh, kv, batch) : sweep_ctas_per_sm_f32(sh, kv, batch);
+    if (precision == ASM_FP64)
+        return sh.minb == 2 ? sweep_ctas_per_sm_f64_m2(sh, kv, batch) : sweep_ctas_per_sm_f64_m1(sh, kv, batch);
+    return sh.minb == 2 ? sweep_ctas_per_sm_f32_m2(sh, kv, batch) : sweep_ctas_per_sm_f32_m1(sh, kv, batch);
 }
 
 template <class T>
 bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long long total_warps, int kv,
-                bool batch, int want_consumers)
+                bool batch, int want_consumers, int minb)
 {
+    sh.minb = minb;
     constexpr int kSMs = 152;
     const int TW = 32 / S;
     const int prec = sizeof(T) == 8 ? ASM_FP64 : ASM_MIXED;
@@ -963,9 +967,15 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
     const int TW = 32 / S;
     const long long warps_per_unit = (chains + TW - 1) / TW;
     const bool batch = !h->kids.empty();
+    const long long total_warps = warps_per_unit * (long long)us.size();
+    // register budget: one CTA per SM (up to 255 registers) while one CTA of
+    // consumers per SM holds every chain; two CTAs (128 registers) when there
+    // are more chains than that, except for FP64 with wide blocks, whose chain
+    // state would spill
+    int minb = total_warps > 152LL * kMaxConsumers && !(sizeof(T) == 8 && kv >= 16) ? 2 : 1;
+    if (h->tuned_minb) minb = h->tuned_minb;
     LaunchShape sh{};
-    if (!plan_shape<T>(sh, S, max_rec, max_np, max_M, warps_per_unit * (long long)us.size(), kv, batch,
-                       h->tuned_consumers))
+    if (!plan_shape<T>(sh, S, max_rec, max_np, max_M, total_warps, kv, batch, h->tuned_consumers, minb))
         return ASM_ERR_TOO_LARGE;
     // work items, the costliest problems first (a longest-first queue)
     std::vector<int> order(us.size());
@@ -985,6 +995,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
     h->last_consumers = sh.consumers;
     h->last_ctas = ctas;
     h->last_items = sh.n_items;
+    h->last_minb = sh.minb;
     const size_t rsmem = sizeof(double) * (size_t)max_N;
     if (const int rc = refresh_smem(refresh_all_kernel<T>, rsmem); rc != ASM_OK) return rc;
     // the mixed path refreshes on the tensor cores (3xTF32) unless asked for FP64 CUDA cores
@@ -1003,8 +1014,12 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
     const unsigned n_refresh = (unsigned)(us.size() * chains);
     const SweepParams<T> &p0 = probs[0];   // a single problem's parameters travel by value
     auto sweep = [&](cudaStream_t st) {
-        if constexpr (sizeof(T) == 8) return launch_sweeps_f64(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
-        else return launch_sweeps_f32(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
+        if constexpr (sizeof(T) == 8)
+            return sh.minb == 2 ? launch_sweeps_f64_m2(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st)
+                                : launch_sweeps_f64_m1(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
+        else
+            return sh.minb == 2 ? launch_sweeps_f32_m2(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st)
+                                : launch_sweeps_f32_m1(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
     };
     auto refresh = [&](cudaStream_t st) {
         if constexpr (sizeof(T) == 4) {
@@ -1035,6 +1050,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             key.consumers = sh.consumers;
             key.depth = sh.depth;
             key.n_items = sh.n_items;
+            key.minb = sh.minb;
             key.refresh_smem = tc ? refresh_tc_smem(max_bn) + 1 : rsmem;
             key.seed = p0.seed;   // by value in a single problem's launch
             key.problem_id = p0.problem_id;
@@ -1473,14 +1489,14 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
 }
 
 int asm_tune(asm_problem *p, int chains, int precision, void *d_workspace, size_t workspace_bytes, void *stream,
-             int *team_out, int *consumers_out)
+             int *team_out, int *consumers_out, int *min_blocks_out)
 {
     if (!p || chains < 1 || (precision != ASM_FP64 && precision != ASM_MIXED)) return ASM_ERR_ARG;
     const RunLayout RL = run_layout(p, chains, precision);
     if (!d_workspace || workspace_bytes < RL.total || ((uintptr_t)d_workspace & 255)) return ASM_ERR_WORKSPACE;
     if (p->ev_used && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
     bind_workspace(p, d_workspace, workspace_bytes, RL, (cudaStream_t)stream);
-    const int team0 = p->team, cons0 = p->tuned_consumers;
+    const int team0 = p->team, cons0 = p->tuned_consumers, minb0 = p->tuned_minb;
     const bool timing0 = p->timing;
     p->timing = false;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1488,15 +1504,17 @@ int asm_tune(asm_problem *p, int chains, int precision, void *d_workspace, size_
         if (e0) cudaEventDestroy(e0);
         return ASM_ERR_CUDA;
     }
-    int best_team = team0, best_cons = cons0, rc = ASM_OK;
+    int best_team = team0, best_cons = cons0, best_minb = minb0, rc = ASM_OK;
     float best = 0.f;
     bool any = false;
     const int teams[] = {32, 16, 8};
     const int conss[] = {0, 2, 3, 4, 5, 6, 7};   // 0: the built-in heuristic
-    for (int S : teams) {
-        for (int c : conss) {
+    for (int trial = 0; trial < 3 * 7 * 2; ++trial) {
+        const int S = teams[trial / 14], c = conss[(trial / 2) % 7], mb = 1 + trial % 2;
+        {
             p->team = S;
             p->tuned_consumers = c;
+            p->tuned_minb = mb;
             // fresh chains, one sweep to warm up, then the timed sweeps
             rc = start_chains(p, chains, precision, 0x74756e65ull, false);
             if (rc != ASM_OK) break;
@@ -1519,6 +1537,7 @@ int asm_tune(asm_problem *p, int chains, int precision, void *d_workspace, size_
                 best = ms;
                 best_team = S;
                 best_cons = c;
+                best_minb = mb;
                 any = true;
             }
         }
@@ -1533,12 +1552,15 @@ int asm_tune(asm_problem *p, int chains, int precision, void *d_workspace, size_
     if (rc != ASM_OK || !any) {
         p->team = team0;
         p->tuned_consumers = cons0;
+        p->tuned_minb = minb0;
         return rc != ASM_OK ? rc : ASM_ERR_TOO_LARGE;
     }
     p->team = best_team;
     p->tuned_consumers = best_cons;
+    p->tuned_minb = best_minb;
     if (team_out) *team_out = best_team;
     if (consumers_out) *consumers_out = best_cons;
+    if (min_blocks_out) *min_blocks_out = best_minb;
     return ASM_OK;
 }
 
@@ -1715,6 +1737,7 @@ int asm_status(asm_problem *p, asm_stats *out)
     out->consumers_per_cta = p->last_consumers;
     out->ctas = p->last_ctas;
     out->work_items = p->last_items;
+    out->min_blocks = p->last_minb;
     return ASM_OK;
 }
 

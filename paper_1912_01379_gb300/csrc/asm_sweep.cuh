@@ -789,8 +789,8 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
 // grid constant p0.  Several: each item's parameters are copied from probs
 // into shared memory.
 // --------------------------------------------------------------------------
-template <class T, int KV, bool BATCH>
-__global__ void __launch_bounds__(32 * (kMaxConsumers + 1), 1) sweep_kernel(const __grid_constant__ SweepParams<T> p0,
+template <class T, int KV, bool BATCH, int MINB>
+__global__ void __launch_bounds__(32 * (kMaxConsumers + 1), MINB) sweep_kernel(const __grid_constant__ SweepParams<T> p0,
                                                     const SweepParams<T> *__restrict__ probs,
                                                     const WorkItem *__restrict__ items, RunCtrl *ctrl,
                                                     const __grid_constant__ LaunchShape shape)
@@ -835,42 +835,43 @@ __global__ void __launch_bounds__(32 * (kMaxConsumers + 1), 1) sweep_kernel(cons
     }
 }
 
-template <class T, int KV, bool BATCH>
+template <class T, int KV, bool BATCH, int MINB>
 cudaError_t launch_sweep_kernel(const SweepParams<T> &p0, const SweepParams<T> *probs, const WorkItem *items,
                                 RunCtrl *ctrl, const LaunchShape &shape, int ctas, cudaStream_t stream)
 {
     const size_t smem = (size_t)shape.off_stages + (size_t)shape.depth * shape.stage_bytes;
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, KV, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, KV, BATCH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    sweep_kernel<T, KV, BATCH><<<(unsigned)ctas, 32 * (shape.consumers + 1), smem, stream>>>(p0, probs, items, ctrl,
+    sweep_kernel<T, KV, BATCH, MINB><<<(unsigned)ctas, 32 * (shape.consumers + 1), smem, stream>>>(p0, probs, items, ctrl,
                                                                                              shape);
     return cudaGetLastError();
 }
 
-template <class T, int KV, bool BATCH>
+template <class T, int KV, bool BATCH, int MINB>
 int sweep_ctas_per_sm(const LaunchShape &shape)
 {
     const size_t smem = (size_t)shape.off_stages + (size_t)shape.depth * shape.stage_bytes;
-    if (cudaFuncSetAttribute(sweep_kernel<T, KV, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(sweep_kernel<T, KV, BATCH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, KV, BATCH>, 32 * (shape.consumers + 1),
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, KV, BATCH, MINB>, 32 * (shape.consumers + 1),
                                                       smem) != cudaSuccess)
         return 0;
     return n;
 }
 
-// dispatch over the register tile (kv) and the batch flag
-template <class T, int... KVs>
+// dispatch over the register tile (kv) and the batch flag, for one residency
+// MINB (CTAs per SM the registers are budgeted for)
+template <class T, int MINB, int... KVs>
 struct SweepDispatch {
     static cudaError_t launch(const SweepParams<T> &p0, const SweepParams<T> *probs, const WorkItem *items,
                               RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch, int ctas, cudaStream_t s)
     {
         cudaError_t e = cudaErrorInvalidValue;
-        ((kv == KVs ? (e = batch ? launch_sweep_kernel<T, KVs, true>(p0, probs, items, ctrl, shape, ctas, s)
-                                 : launch_sweep_kernel<T, KVs, false>(p0, probs, items, ctrl, shape, ctas, s),
+        ((kv == KVs ? (e = batch ? launch_sweep_kernel<T, KVs, true, MINB>(p0, probs, items, ctrl, shape, ctas, s)
+                                 : launch_sweep_kernel<T, KVs, false, MINB>(p0, probs, items, ctrl, shape, ctas, s),
                        0)
                     : 0),
          ...);
@@ -879,7 +880,8 @@ struct SweepDispatch {
     static int per_sm(const LaunchShape &shape, int kv, bool batch)
     {
         int n = 0;
-        ((kv == KVs ? (n = batch ? sweep_ctas_per_sm<T, KVs, true>(shape) : sweep_ctas_per_sm<T, KVs, false>(shape),
+        ((kv == KVs ? (n = batch ? sweep_ctas_per_sm<T, KVs, true, MINB>(shape)
+                                 : sweep_ctas_per_sm<T, KVs, false, MINB>(shape),
                        0)
                     : 0),
          ...);

@@ -1,19 +1,20 @@
-// FP32 chain state (the mixed-precision path): instantiations of the sweep kernel.
+// FP32 chain state (the mixed-precision path): instantiations of the sweep kernel budgeted for 1 CTA per SM
+// (up to 255 registers per thread).
 #include "asm_sweep.cuh"
 
 namespace asmgb {
 
-using DispatchF32 = SweepDispatch<float, 1, 2, 4, 8, 16>;
+using Dispatch = SweepDispatch<float, 1, 1, 2, 4, 8, 16>;
 
-cudaError_t launch_sweeps_f32(const SweepParams<float> &p0, const SweepParams<float> *probs, const WorkItem *items,
-                              RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch, int ctas, cudaStream_t s)
+cudaError_t launch_sweeps_f32_m1(const SweepParams<float> &p0, const SweepParams<float> *probs, const WorkItem *items,
+                                RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch, int ctas, cudaStream_t s)
 {
-    return DispatchF32::launch(p0, probs, items, ctrl, shape, kv, batch, ctas, s);
+    return Dispatch::launch(p0, probs, items, ctrl, shape, kv, batch, ctas, s);
 }
 
-int sweep_ctas_per_sm_f32(const LaunchShape &shape, int kv, bool batch)
+int sweep_ctas_per_sm_f32_m1(const LaunchShape &shape, int kv, bool batch)
 {
-    return DispatchF32::per_sm(shape, kv, batch);
+    return Dispatch::per_sm(shape, kv, batch);
 }
 
 }  // namespace asmgb

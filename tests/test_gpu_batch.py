@@ -117,13 +117,13 @@ def test_tuned_shape_changes_no_result(prec):
     b = asm.Batch([_spec(p) for p in probs])
     b.sample(64, 0, 70, 3, precision=prec)
     ref = [b.average(k)["mean_fbar"] for k in range(len(probs))]
-    team, cons = b.tune(64, precision=prec)
-    assert team in (8, 16, 32) and cons in (0, 2, 3, 4, 5, 6, 7)
+    team, cons, minb = b.tune(64, precision=prec)
+    assert team in (8, 16, 32) and cons in (0, 2, 3, 4, 5, 6, 7) and minb in (1, 2)
     with pytest.raises(asm.ASMError):   # the trial chains replaced the state
         b.sample(64, 0, 1, 3, precision=prec, cont=True)
     b.sample(64, 0, 70, 3, precision=prec)
     st = b.status()
-    assert st["team_lanes"] == team
+    assert st["team_lanes"] == team and st["min_blocks"] == minb
     for k in range(len(probs)):
         assert np.array_equal(b.average(k)["mean_fbar"], ref[k]), (k, team, cons)
 
