@@ -12,8 +12,10 @@ the mixed FP32/FP64 path.  `value` = chain-mode updates per second
 on the device; `e2e` runs asm_setup from host arrays + asm_sample + asm_average
 (device->host results) per step.  The plain FP64 path and ESS/s of <A(omega)>
 are reported beside it, and, as side measurements outside the timed region,
-the batching workload (256 uneven problems in one handle) and the grid-size
-sweep (N_omega 250..2000, 8192 chains), each in both paths.
+the batching workload (256 uneven problems in one handle), the grid-size
+sweep (N_omega 250..2000, 8192 chains), each in both paths, and ESS/s of the
+blocked-modes problem under four partition schemes (modes, components, the
+workload's two levels, the full hierarchy).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -61,6 +63,8 @@ def _args():
                     help="sweeps of the batching side measurement (0: skip)")
     ap.add_argument("--grid-sweeps", type=int, default=64,
                     help="sweeps per N_omega of the grid-size side measurement (0: skip)")
+    ap.add_argument("--hierarchy-sweeps", type=int, default=3000,
+                    help="sweeps per partition scheme of the hierarchy side measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -260,6 +264,30 @@ def grid_side(args, asm, torch, stream):
     return {"workload": "grid_sweep_fermionic_b50_Ntau400_uniform_16blocks_8192chains", "rows": rows}
 
 
+def hierarchy_side(args, asm, torch, stream):
+    """The blocked-modes workload's problem under four partition schemes (Sec.
+    IV): modes only (one block), components only (one point per block), the
+    workload's {global, 8 x 50} levels, and the full hierarchy of
+    asm_partition_hierarchy.  Mixed path, 1024 chains; updates/s and ESS/s
+    (min over the grid) after a burn-in."""
+    p = W.blocked_modes_problem()
+    schemes = {"modes": [[0]], "components": [np.arange(p.N)], "global_8x50": p.levels,
+               "hierarchy": asm.partition_hierarchy(p.N)}
+    chains, burn, sweeps = 1024, 500, args.hierarchy_sweeps
+    out = {"workload": WORKLOAD, "chains": chains, "burn_in": burn, "sweeps": sweeps}
+    for name, levels in schemes.items():
+        gp = asm.Problem(p.K, p.G, p.C, levels, w=p.w)
+        gp.sample(chains, 0, 1, 31)
+        t = _timed(torch, stream, lambda: gp.sample(chains, burn, sweeps, 32))
+        r = gp.average()
+        out[name] = {"levels": len(levels), "blocks": int(sum(len(l) for l in levels)),
+                     "updates_per_s": chains * (burn + sweeps) * p.N / t,
+                     "ess_min": float(np.nanmin(r["ess"])), "ess_median": float(np.nanmedian(r["ess"])),
+                     "ess_per_s": float(np.nanmin(r["ess"])) / t}
+        del gp
+    return out
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle is the reference arm for this method."""
     ws, rank, _ = _dist()
@@ -399,6 +427,7 @@ def main():
 
     batch = batch_side(args, asm, torch, stream) if (args.batch_sweeps > 0 and rank == 0) else None
     grid = grid_side(args, asm, torch, stream) if (args.grid_sweeps > 0 and rank == 0) else None
+    hier = hierarchy_side(args, asm, torch, stream) if (args.hierarchy_sweeps > 0 and rank == 0) else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -425,6 +454,7 @@ def main():
             "e2e": e2e,
             "batch": batch,
             "grid_sweep": grid,
+            "partition_schemes": hier,
             "gpu_launches": int(sweep_launches + other_launches + args.steps),
             "clocks": clocks,
         }

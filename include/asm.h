@@ -138,6 +138,19 @@ int asm_setup(const asm_desc *d, asm_problem **out);
  * single problems (ASM_ERR_ARG on a batch).  On failure nothing is kept. */
 int asm_setup_batch(int n, const asm_desc *d, asm_problem **out);
 
+/* Partition hierarchy of blocked modes sampling (Sec. IV.C and Fig. blocks):
+ * level 0 is the whole grid (modes sampling); level l >= 1 splits the N grid
+ * points into blocks of nominal width w_l = N / 2^l, boundaries at
+ * round(k w_l + s_l) with s_l = w_l / 2 on even levels l >= 2 and 0 on odd
+ * ones (the shift keeps every other level from having a boundary at the centre
+ * of the grid); the last level has one point per block (components sampling).
+ * Levels equal to the one above are left out.  Out: *n_levels (at most 33),
+ * level_nblocks[l] (capacity 33), *total_blocks and, unless block_start is NULL,
+ * the concatenated block starts of every level (capacity *total_blocks, so a
+ * first call with block_start = NULL gives the size).  The result is a valid
+ * asm_desc partition.  Host only; ASM_ERR_ARG for N < 1 or NULL outputs. */
+int asm_partition_hierarchy(int N, int *n_levels, int *level_nblocks, int *block_start, int *total_blocks);
+
 /* Number of problems of a handle (1 for asm_setup). */
 int asm_problem_count(const asm_problem *p);
 

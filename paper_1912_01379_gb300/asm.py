@@ -51,7 +51,7 @@ class asm_stats(ct.Structure):
 EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",
            "asm_status", "asm_destroy", "asm_error_string", "asm_sample_noalloc", "asm_set_stream_ids",
            "asm_checkpoint", "asm_restore", "asm_backward", "asm_setup_batch", "asm_problem_count",
-           "asm_average_at", "asm_tune"]
+           "asm_average_at", "asm_tune", "asm_partition_hierarchy"]
 ASM_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
@@ -109,8 +109,29 @@ def load(build_if_missing: bool = True):
     L.asm_tune.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_size_t, ct.c_void_p,
                            ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
     L.asm_tune.restype = ct.c_int
+    L.asm_partition_hierarchy.argtypes = [ct.c_int, _ip, _ip, _ip, _ip]
+    L.asm_partition_hierarchy.restype = ct.c_int
     _lib = L
     return L
+
+
+def partition_hierarchy(N):
+    """asm_partition_hierarchy: the levels (arrays of block starts) of the
+    blocked-modes hierarchy on N grid points, from the whole grid down to one
+    point per block.  Host-side, needs no GPU."""
+    L = load()
+    nl, tot = ct.c_int(0), ct.c_int(0)
+    nb = np.zeros(64, dtype=np.int32)
+    _check(L.asm_partition_hierarchy(int(N), ct.byref(nl), nb.ctypes.data_as(_ip), None, ct.byref(tot)),
+           "asm_partition_hierarchy")
+    bs = np.zeros(max(tot.value, 1), dtype=np.int32)
+    _check(L.asm_partition_hierarchy(int(N), ct.byref(nl), nb.ctypes.data_as(_ip), bs.ctypes.data_as(_ip),
+                                     ct.byref(tot)), "asm_partition_hierarchy")
+    out, o = [], 0
+    for l in range(nl.value):
+        out.append(bs[o:o + nb[l]].copy())
+        o += nb[l]
+    return out
 
 
 class ASMError(RuntimeError):

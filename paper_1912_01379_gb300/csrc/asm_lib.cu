@@ -1366,6 +1366,43 @@ size_t asm_workspace_bytes(const asm_problem *p, int chains, int precision)
     return run_layout(p, chains, precision).total;
 }
 
+int asm_partition_hierarchy(int N, int *n_levels, int *level_nblocks, int *block_start, int *total_blocks)
+{
+    if (N < 1 || !n_levels || !level_nblocks || !total_blocks) return ASM_ERR_ARG;
+    std::vector<std::vector<int>> levels;
+    levels.push_back({0});   // the whole grid: modes sampling
+    int depth = 0;
+    while ((1LL << depth) < N) ++depth;   // ceil(log2 N)
+    for (int l = 1; l < depth; ++l) {
+        const double w = (double)N / (double)(1LL << l);
+        const double shift = (l % 2 == 0) ? 0.5 * w : 0.0;   // every other level, half a block
+        std::vector<int> starts{0};
+        for (long long k = 0;; ++k) {
+            const double x = (double)k * w + shift;
+            if (x >= (double)N) break;
+            const int b = (int)std::floor(x + 0.5);
+            if (b > starts.back() && b < N) starts.push_back(b);
+        }
+        if (starts != levels.back()) levels.push_back(starts);
+    }
+    if (N > 1) {   // one grid point per block: components sampling
+        std::vector<int> starts(N);
+        for (int n = 0; n < N; ++n) starts[n] = n;
+        if (starts != levels.back()) levels.push_back(starts);
+    }
+    long long total = 0;
+    for (const auto &l : levels) total += (long long)l.size();
+    *n_levels = (int)levels.size();
+    *total_blocks = (int)total;
+    for (size_t l = 0; l < levels.size(); ++l) level_nblocks[l] = (int)levels[l].size();
+    if (block_start) {
+        long long o = 0;
+        for (const auto &l : levels)
+            for (int b : l) block_start[o++] = b;
+    }
+    return ASM_OK;
+}
+
 int asm_problem_count(const asm_problem *p)
 {
     if (!p) return ASM_ERR_ARG;
