@@ -229,6 +229,22 @@ int asm_backward(asm_problem *p, const double *v, double *grad_G, double *grad_t
 /* asm_average for problem k of a handle (k = 0 for a single problem). */
 int asm_average_at(asm_problem *p, int k, double *mean_A, double *sem_A, double *ess, double *mean_fbar);
 
+/* Monte Carlo error of <fbar> for problem k of a handle (synchronises), by
+ * binning (Flyvbjerg and Petersen 1989; not in the paper): the kept sweeps of
+ * every chain are cut into bins of 64 sweeps aligned to multiples of 64 in the
+ * absolute sweep index (only bins wholly after the burn-in count), merged
+ * pairwise over 8 levels (bins of 64 ... 8192 sweeps); at level l the squared
+ * error of the grand mean is the variance of all chains' level-l bin means
+ * over their number.  sem_fbar^2 (N) = the largest of these over the levels
+ * with at least two bins per chain and of the squared spread of the chain
+ * means (asm_average's error); ess (N) = posterior variance / sem_fbar^2.
+ * A drift that all chains share (a common start not yet forgotten) raises the
+ * binned error although it hides from the chain spread.  Optional outputs:
+ * sigma2_levels (8 x N, NaN where a level has fewer than two bins in all) and
+ * bins_per_chain (8).  Any argument but p may be NULL.  ASM_ERR_STATE before a
+ * run with kept sweeps. */
+int asm_mc_error(asm_problem *p, int k, double *ess, double *sem_fbar, double *sigma2_levels, int *bins_per_chain);
+
 /* Current chain states (synchronises): f (chains x N, FP64 copy of fbar) and
  * chi2 (chains) = |r~|^2 of the residual the sampler tracks; either may be NULL. */
 int asm_chain_state(asm_problem *p, double *f, double *chi2);

@@ -241,3 +241,56 @@ def summarize(S1, S2, kept, w=None):
         out["mean_A"] = mean / w
         out["sem_A"] = sem / w
     return out
+
+
+BIN_SWEEPS = 64      # sweeps per level-0 bin (aligned to absolute sweep indices)
+BIN_LEVELS = 8       # doubling levels: bins of 64, 128, ..., 8192 sweeps
+
+
+def binning(trace, sweep0, burn_in, b0=BIN_SWEEPS, levels=BIN_LEVELS):
+    """Monte Carlo error of the mean of fbar by binning (Flyvbjerg and Petersen,
+    J. Chem. Phys. 91, 461 (1989)): the kept sweeps of every chain are cut into
+    bins of b0 sweeps aligned to multiples of b0 in the absolute sweep index
+    (only bins lying wholly after the burn-in count), neighbouring bins are
+    merged pairwise level by level, and at level k the squared error of the
+    grand mean is the variance of the level-k bin means over all chains'
+    bins divided by their number.
+
+    trace: chains x sweeps x N states after each sweep, the first one being
+    absolute sweep `sweep0`; burn_in: absolute index of the first kept sweep.
+    Returns (sigma2 per level, levels x N; bins per chain per level)."""
+    trace = np.asarray(trace, dtype=np.float64)
+    C, T, N = trace.shape
+    first = -(-max(burn_in, sweep0) // b0) * b0          # first bin start inside the kept range
+    nb0 = (sweep0 + T - first) // b0 if sweep0 + T > first else 0
+    sig2 = np.full((levels, N), np.nan)
+    counts = np.zeros(levels, dtype=np.int64)
+    if nb0 <= 0:
+        return sig2, counts
+    x = trace[:, first - sweep0: first - sweep0 + nb0 * b0, :].reshape(C, nb0, b0, N).mean(axis=2)
+    for k in range(levels):
+        m = x.shape[1]
+        counts[k] = m
+        if m >= 1:
+            means = x.reshape(C * m, N)
+            n = means.shape[0]
+            if n > 1:
+                sig2[k] = means.var(axis=0, ddof=1) / n
+        if m < 2:
+            break
+        x = 0.5 * (x[:, 0:2 * (m // 2):2, :] + x[:, 1:2 * (m // 2):2, :])
+    return sig2, counts
+
+
+def mc_error(trace, sweep0, burn_in, S1, S2, kept):
+    """The error estimate the library reports: sigma^2 = the largest binning
+    level with at least two bins per chain, or the squared spread of the chain
+    means if that is larger; ESS = posterior variance / sigma^2."""
+    sig2, counts = binning(trace, sweep0, burn_in)
+    s = summarize(S1, S2, kept)
+    best = np.array(s["sem_fbar"]) ** 2
+    for k in range(len(counts)):
+        if counts[k] >= 2:
+            best = np.fmax(best, sig2[k])
+    ess = np.maximum(s["var_fbar"], 0.0) / np.maximum(best, 1e-300)
+    return {"sigma2": best, "ess": ess, "sigma2_levels": sig2, "bins_per_chain": counts}

@@ -22,6 +22,8 @@ ASM_SAMPLE_TIMING = 2
 ASM_SAMPLE_MOMENTS = 4
 ASM_SAMPLE_REFRESH_FP64 = 8
 ASM_SNAPSHOT_EVERY = 8
+BIN_SWEEPS = 64      # binning: level-0 bin length in sweeps
+BIN_LEVELS = 8       # binning: doubling levels
 
 _dp = ct.POINTER(ct.c_double)
 _ip = ct.POINTER(ct.c_int)
@@ -51,7 +53,7 @@ class asm_stats(ct.Structure):
 EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",
            "asm_status", "asm_destroy", "asm_error_string", "asm_sample_noalloc", "asm_set_stream_ids",
            "asm_checkpoint", "asm_restore", "asm_backward", "asm_setup_batch", "asm_problem_count",
-           "asm_average_at", "asm_tune", "asm_partition_hierarchy"]
+           "asm_average_at", "asm_tune", "asm_partition_hierarchy", "asm_mc_error"]
 ASM_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
@@ -111,6 +113,8 @@ def load(build_if_missing: bool = True):
     L.asm_tune.restype = ct.c_int
     L.asm_partition_hierarchy.argtypes = [ct.c_int, _ip, _ip, _ip, _ip]
     L.asm_partition_hierarchy.restype = ct.c_int
+    L.asm_mc_error.argtypes = [ct.c_void_p, ct.c_int, _dp, _dp, _dp, _ip]
+    L.asm_mc_error.restype = ct.c_int
     _lib = L
     return L
 
@@ -243,6 +247,17 @@ class _Handle:
     def set_stream_ids(self, problem_id=0, chain_offset=0):
         _check(load().asm_set_stream_ids(self._h, ct.c_uint64(problem_id), ct.c_uint64(chain_offset)),
                "asm_set_stream_ids")
+
+    def mc_error(self, k=0):
+        """asm_mc_error: binned Monte Carlo error of <fbar> of problem k:
+        ess, sem_fbar (N each), sigma2_levels (8 x N), bins_per_chain (8)."""
+        N = self.shapes[k][1] if hasattr(self, "shapes") else self.N
+        ess, sem = np.zeros(N), np.zeros(N)
+        lv = np.zeros((BIN_LEVELS, N))
+        bins = np.zeros(BIN_LEVELS, dtype=np.int32)
+        _check(load().asm_mc_error(self._h, k, _dptr(ess), _dptr(sem), _dptr(lv), bins.ctypes.data_as(_ip)),
+               "asm_mc_error")
+        return {"ess": ess, "sem_fbar": sem, "sigma2_levels": lv, "bins_per_chain": bins}
 
     def status(self):
         st = asm_stats()

@@ -58,6 +58,11 @@ struct SweepParams {
     T *F; int ldF;                    // chain states, chains x ldF
     T *R; int ldR;                    // tracked residuals, chains x ldR
     double *S1, *S2;                  // sums of f and f^2, chains x N
+    // binning of the Monte Carlo error (every kBinSweeps sweeps): S1 at the last bin
+    // boundary (chains x N), per chain and level the pending half of a bin pair and the
+    // sums of the bin means and their squares (chains x kBinLevels x N), level-0 bins per chain
+    double *S1p, *bpend, *bacc1, *bacc2;
+    int *bcount;
     int chains;
     unsigned long long seed, problem_id;
     unsigned long long chain_offset;  // global id of local chain 0 (Philox key word)
@@ -132,6 +137,11 @@ cudaError_t launch_split_k(const double *KtT, int M, int N, int ldK, float *Khi,
 int sweep_ctas_per_sm_f32(const LaunchShape &shape, int kv, bool batch);
 int sweep_ctas_per_sm_f64(const LaunchShape &shape, int kv, bool batch);
 // Largest supported kv per precision.
+// Binning: bins of kBinSweeps kept sweeps aligned to multiples of kBinSweeps in
+// the absolute sweep index (the refresh period), merged pairwise over kBinLevels
+// levels (bins of 64 ... 8192 sweeps).
+constexpr int kBinSweeps = 64;
+constexpr int kBinLevels = 8;
 // Consumer warps per CTA: at most 7, so that a CTA (consumers + the producer)
 // has at most 8 warps, two per SM sub-partition, and a thread may hold up to
 // 255 registers (9 warps would put three on one sub-partition: 168).

@@ -135,6 +135,61 @@ __global__ void ctrl_kernel(RunCtrl *c, long long sweep0, long long nsweeps, lon
     }
 }
 
+// Binning at a bin boundary (the end of a launch whose range ends at a multiple
+// of kBinSweeps): CTA b handles chain b % chains of problem b / chains.  The sum
+// of the last kBinSweeps sweeps is S1 - S1p; if the bin lies wholly after the
+// burn-in its mean enters level 0, and pairs of level-k bin means merge into a
+// level-(k+1) bin (level-k bin c, counted from 1, is the first of a pair when c
+// is odd).  Sums of the bin means and their squares per level and grid point.
+template <class T>
+__global__ void bin_kernel(const SweepParams<T> *__restrict__ probs, int chains, const RunCtrl *ctrl)
+{
+    __shared__ int s_nb;
+    const SweepParams<T> &p = probs[blockIdx.x / chains];
+    const int q = blockIdx.x % chains;
+    const long long s_end = ctrl->sweep0 + ctrl->nsweeps;
+    const bool complete = s_end % kBinSweeps == 0 && s_end - kBinSweeps >= ctrl->burn_in;
+    if (threadIdx.x == 0) s_nb = p.bcount[q] + (complete ? 1 : 0);
+    __syncthreads();
+    const int nb = s_nb;
+    const int N = p.N;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const size_t i = (size_t)q * N + n;
+        const double s1 = p.S1[i];
+        double x = (s1 - p.S1p[i]) * (1.0 / kBinSweeps);
+        p.S1p[i] = s1;
+        if (!complete) continue;
+        for (int k = 0; k < kBinLevels; ++k) {
+            const size_t j = ((size_t)q * kBinLevels + k) * N + n;
+            p.bacc1[j] += x;
+            p.bacc2[j] += x * x;
+            if (k + 1 == kBinLevels || ((nb >> k) & 1)) {
+                if ((nb >> k) & 1) p.bpend[j] = x;
+                break;
+            }
+            x = 0.5 * (p.bpend[j] + x);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && complete) p.bcount[q] = nb;
+}
+
+// Sums over chains, in chain order, of the binning sums of one problem:
+// out[0][k][n] = sum of bin means, out[1][k][n] = sum of their squares.
+__global__ void bin_reduce_kernel(const double *__restrict__ acc1, const double *__restrict__ acc2, int chains,
+                                  int N, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;   // k * N + n
+    if (i >= kBinLevels * N) return;
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < chains; ++q) {
+        a += acc1[(size_t)q * kBinLevels * N + i];
+        b += acc2[(size_t)q * kBinLevels * N + i];
+    }
+    out[i] = a;
+    out[(size_t)kBinLevels * N + i] = b;
+}
+
 // Per grid point: mean over chains and kept sweeps, the spread of the chain
 // means (two passes) and the second moment.
 __global__ void reduce_kernel(const double *S1, const double *S2, int chains, int N, double kept,
@@ -285,6 +340,7 @@ struct WsLayout {
     size_t counters, F, R, S1, S2, chi2;
     size_t Sff, Sf, Sfs, Ss, Gtmp, Y, Sq;   // snapshot moments for the backward pass
     size_t shift, kshift, D;                // centring of the snapshots
+    size_t S1p, bpend, bacc1, bacc2, bcount; // binning of the Monte Carlo error
     size_t total;
     int ldF, ldR;
 };
@@ -331,6 +387,7 @@ struct asm_problem {
     size_t ws_bytes = 0;
     int chains = 0, precision = -1, team = 32;
     long long sweeps_done = 0, kept = 0;
+    long long kept_since = 0;   // every sweep from this one on has been accumulated
     unsigned long long seed = 0;
     unsigned long long problem_id = 0, chain_offset = 0;   // Philox identities of the run
     unsigned long long next_problem_id = 0, next_chain_offset = 0;
@@ -393,6 +450,12 @@ WsLayout ws_layout(const asm_problem *p, int chains, int precision)
     L.shift = off; off = align_up(off + N * 8, 256);
     L.kshift = off; off = align_up(off + (size_t)p->M * std::max<size_t>(P, 1) * 8, 256);
     L.D = off; off = align_up(off + (size_t)chains * L.ldF * es, 256);
+    const size_t binned = (size_t)chains * kBinLevels * N * 8;
+    L.S1p = off; off = align_up(off + (size_t)chains * N * 8, 256);
+    L.bpend = off; off = align_up(off + binned, 256);
+    L.bacc1 = off; off = align_up(off + binned, 256);
+    L.bacc2 = off; off = align_up(off + binned, 256);
+    L.bcount = off; off = align_up(off + (size_t)chains * 4, 256);
     L.total = off;
     return L;
 }
@@ -768,6 +831,11 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.ldK = p->ldK;
     sp.gt = p->d_gt;
     sp.chi2 = (double *)(ws + L.chi2);
+    sp.S1p = (double *)(ws + L.S1p);
+    sp.bpend = (double *)(ws + L.bpend);
+    sp.bacc1 = (double *)(ws + L.bacc1);
+    sp.bacc2 = (double *)(ws + L.bacc2);
+    sp.bcount = (int *)(ws + L.bcount);
     sp.f0 = p->f0;
     return sp;
 }
@@ -1021,6 +1089,10 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             return sh.minb == 2 ? launch_sweeps_f32_m2(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st)
                                 : launch_sweeps_f32_m1(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
     };
+    auto binning = [&](cudaStream_t st) {
+        bin_kernel<T><<<n_refresh, 128, 0, st>>>(d_probs, chains, ctrl);
+        return cudaGetLastError();
+    };
     auto refresh = [&](cudaStream_t st) {
         if constexpr (sizeof(T) == 4) {
             if (tc) {
@@ -1064,6 +1136,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
                 ctrl_kernel<<<1, 1, 0, h->cap_stream>>>(ctrl, 0, 0, 0, 1);
                 cudaError_t e = cudaGetLastError();
                 if (e == cudaSuccess) e = sweep(h->cap_stream);
+                if (e == cudaSuccess) e = binning(h->cap_stream);
                 if (e == cudaSuccess) e = refresh(h->cap_stream);
                 cudaGraph_t graph = nullptr;
                 const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
@@ -1082,7 +1155,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             for (long long i = 0; i < whole; ++i)
                 if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) return ASM_ERR_CUDA;
             h->sweep_launches += whole;
-            h->other_launches += 1 + 2 * whole;
+            h->other_launches += 1 + 3 * whole;
             h->graph_replays += whole;
             if (tc) h->tc_refreshes += whole;
             s += whole * kRefreshPeriod;
@@ -1113,8 +1186,9 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             if (rc != ASM_OK) return rc;
         }
         if (s % kRefreshPeriod == 0) {
+            if (binning(h->stream) != cudaSuccess) return ASM_ERR_CUDA;
             if (refresh(h->stream) != cudaSuccess) return ASM_ERR_CUDA;
-            ++h->other_launches;
+            h->other_launches += 2;
             if (tc) ++h->tc_refreshes;
         }
     }
@@ -1134,6 +1208,9 @@ int init_chains(asm_problem *p, const WsLayout &L, int chains)
         return ASM_ERR_CUDA;
     // snapshot moments of the backward pass start at zero
     if (cudaMemsetAsync(ws + L.Sff, 0, L.Gtmp - L.Sff, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
+    // binning state starts empty
+    if (cudaMemsetAsync(ws + L.S1p, 0, L.bcount + (size_t)chains * 4 - L.S1p, p->stream) != cudaSuccess)
+        return ASM_ERR_CUDA;
     p->nsnap = 0;
     if (const int rc = refresh_smem(refresh_kernel<T>, sizeof(double) * p->N); rc != ASM_OK) return rc;
     refresh_kernel<T><<<chains, 128, sizeof(double) * p->N, p->stream>>>(
@@ -1517,7 +1594,12 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
         rc = start_chains(p, chains, precision, seed, moments);
         if (rc != ASM_OK) return rc;
     }
-    const long long s0 = p->sweeps_done, s1 = s0 + burn_in + sweeps, burn_abs = s0 + burn_in;
+    const long long s0 = p->sweeps_done, s1 = s0 + burn_in + sweeps;
+    // first sweep of the unbroken run of kept sweeps: a continuation without burn-in
+    // extends the previous one (bins may straddle the calls)
+    long long burn_abs = s0 + burn_in;
+    if (cont && burn_in == 0) burn_abs = std::min(burn_abs, p->kept_since);
+    p->kept_since = burn_abs;
     rc = precision == ASM_FP64 ? run_all<double>(p, chains, s0, s1, burn_abs)
                                : run_all<float>(p, chains, s0, s1, burn_abs);
     if (rc != ASM_OK) return rc;
@@ -1653,6 +1735,63 @@ int asm_average(asm_problem *p, double *mean_A, double *sem_A, double *ess, doub
         if (mean_A) mean_A[n] = mu / p->w[n];
         if (sem_A) sem_A[n] = std::sqrt(s2) / p->w[n];
         if (ess) ess[n] = s2 > 0.0 ? var / s2 : NAN;
+    }
+    return ASM_OK;
+}
+
+int asm_mc_error(asm_problem *p, int k, double *ess, double *sem_fbar, double *sigma2_levels, int *bins_per_chain)
+{
+    static_assert(kBinSweeps == kRefreshPeriod, "bins close at refresh boundaries");
+    if (!p || k < 0 || k >= asm_problem_count(p)) return ASM_ERR_ARG;
+    asm_problem *u = p->kids.empty() ? p : p->kids[(size_t)k];
+    if (!p->have_run || !u->have_run || u->kept < 1) return ASM_ERR_STATE;
+    {
+        Counters c{};
+        if (read_counters_all(p, &c) != ASM_OK) return ASM_ERR_CUDA;
+        if (c.timeouts) return ASM_ERR_TIMEOUT;
+    }
+    const WsLayout L = ws_layout(u, u->chains, u->precision);
+    const int N = u->N, chains = u->chains;
+    const size_t nk = (size_t)kBinLevels * N;
+    double *d = nullptr;
+    if (cudaMalloc(&d, sizeof(double) * (3 * (size_t)N + 2 * nk)) != cudaSuccess) return ASM_ERR_CUDA;
+    const char *ws = (const char *)u->ws;
+    reduce_kernel<<<(N + 127) / 128, 128, 0, p->stream>>>((const double *)(ws + L.S1), (const double *)(ws + L.S2),
+                                                          chains, N, (double)u->kept, d, d + N, d + 2 * N);
+    bin_reduce_kernel<<<(unsigned)((nk + 127) / 128), 128, 0, p->stream>>>(
+        (const double *)(ws + L.bacc1), (const double *)(ws + L.bacc2), chains, N, d + 3 * N);
+    p->other_launches += 2;
+    std::vector<double> h(3 * (size_t)N + 2 * nk);
+    int nb = 0;
+    int rc = ASM_OK;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h.data(), d, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&nb, ws + L.bcount, sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+        rc = ASM_ERR_CUDA;
+    cudaFree(d);
+    if (rc != ASM_OK) return rc;
+    const double *A1 = h.data() + 3 * N, *A2 = A1 + nk;
+    for (int l = 0; l < kBinLevels; ++l)
+        if (bins_per_chain) bins_per_chain[l] = nb >> l;
+    for (int n = 0; n < N; ++n) {
+        const double mu = h[n], s2 = h[N + n], m2 = h[2 * N + n];
+        const double var = std::max(m2 - mu * mu, 0.0);
+        double best = s2;   // the spread of the chain means
+        for (int l = 0; l < kBinLevels; ++l) {
+            const long long c = nb >> l;                      // level-l bins per chain
+            const double cnt = (double)c * chains;            // level-l bins in all
+            double sig2 = NAN;
+            if (cnt > 1.0) {
+                const double m = A1[(size_t)l * N + n] / cnt;
+                const double v = std::max(A2[(size_t)l * N + n] / cnt - m * m, 0.0) * cnt / (cnt - 1.0);
+                sig2 = v / cnt;
+                if (c >= 2) best = std::max(best, sig2);
+            }
+            if (sigma2_levels) sigma2_levels[(size_t)l * N + n] = sig2;
+        }
+        if (sem_fbar) sem_fbar[n] = std::sqrt(best);
+        if (ess) ess[n] = best > 0.0 ? var / best : NAN;
     }
     return ASM_OK;
 }
