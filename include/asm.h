@@ -124,7 +124,9 @@ typedef struct {
  * Sec. IV.B-C: SVD K~_b = U_b D_b V_b^T of every block of every level, in FP64
  * on the device).  Singular vectors get the sign that makes the largest
  * |component| of each V_j positive; d <= d_1 max(M,n_b) 2^-52 counts as a zero
- * mode.  On success *out receives a new handle (free with asm_destroy). */
+ * mode, and so does d <= d_1 max(M,n_b) 2^-40 when V_j changes sign (below
+ * that level U_j = K~ V_j / d_j is not resolvable in FP64 while the likelihood
+ * is flat along V_j over its positivity interval).  On success *out receives a new handle (free with asm_destroy). */
 int asm_setup(const asm_desc *d, asm_problem **out);
 
 /* Set-up of n independent problems as one batch handle (each problem as in

@@ -15,7 +15,8 @@
  *     relative to hi - lo: Gauss-Legendre + Newton on intervals narrower than
  *     the Gaussian's curvature, Phi^{-1} in the centre, log Q in the tails.
  *  R2 zero modes (d = 0, Sec. IV.B) are flat on their interval; singular
- *     values d <= d_1 max(M, n) 2^-52 count as zero.
+ *     values d <= d_1 max(M, n) 2^-52 count as zero, and so do those up to
+ *     d_1 max(M, n) 2^-40 whose vector changes sign (R2).
  *  R3 the bounds of Eq. modeLimits are used as delta in [max_{V>0} -f/V,
  *     min_{V<0} -f/V]; entries |V| < 2^-40 max|V| are left out of the bounds;
  *     after the move f is clamped at 0 so A >= 0 holds exactly.
@@ -404,18 +405,18 @@ static int ora_block_svd(const ora_problem *p, ora_block *b)
     b->d = (double *)calloc(n, sizeof(double));
     b->V = (double *)malloc(sizeof(double) * (size_t)n * n);
     b->U = (double *)calloc((size_t)b->np * M, sizeof(double));
-    double thr = s[0] * (double)(M > n ? M : n) * 0x1p-52;
-    for (int j = 0; j < n; ++j) {
-        b->d[j] = (j < b->np && s[j] > thr) ? s[j] : 0.0;
+    /* R2 zero modes.  d <= d_1 max(M,n) 2^-52 is numerically zero.  Up to
+     * d_1 max(M,n) 2^-40 the left vector U_j = K~ V_j / d_j cannot be formed
+     * in FP64 to better than about 2^-52 d_1 / d_j, which moves the
+     * conditional mean by a visible fraction of its width, while the
+     * likelihood varies by only exp(-(d Delta)^2/2) ~ 1 over the positivity
+     * interval Delta: such a mode is sampled flat when its vector changes sign
+     * (so that the interval is finite) and keeps its Gaussian otherwise. */
+    const double dmax = (double)(M > n ? M : n);
+    const double thr0 = s[0] * dmax * 0x1p-52, thr = s[0] * dmax * 0x1p-40;
+    for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) b->V[(size_t)j * n + i] = V[(size_t)i * n + j];
-        if (j < b->np && b->d[j] > 0.0)
-            for (int m = 0; m < M; ++m) b->U[(size_t)j * M + m] = U[(size_t)m * n + j];
-    }
-    free(A); free(s); free(U); free(V);
-    /* R2 properness: along a zero mode the interval must be finite on both
-     * sides, i.e. the mode vector must change sign. */
     for (int j = 0; j < n; ++j) {
-        if (b->d[j] > 0.0) continue;
         const double *v = b->V + (size_t)j * n;
         double vmax = 0.0;
         for (int i = 0; i < n; ++i) vmax = fmax(vmax, fabs(v[i]));
@@ -425,8 +426,14 @@ static int ora_block_svd(const ora_problem *p, ora_block *b)
             if (v[i] > 0.0) pos = 1;
             if (v[i] < 0.0) neg = 1;
         }
-        if (!(pos && neg)) return -4;
+        const double sj = j < b->np ? s[j] : 0.0;
+        const int zero = sj <= thr0 || (sj <= thr && pos && neg);
+        if (zero && !(pos && neg)) { free(A); free(s); free(U); free(V); return -4; }   /* improper */
+        b->d[j] = zero ? 0.0 : sj;
+        if (!zero)
+            for (int m = 0; m < M; ++m) b->U[(size_t)j * M + m] = U[(size_t)m * n + j];
     }
+    free(A); free(s); free(U); free(V);
     return 0;
 }
 

@@ -616,8 +616,13 @@ int device_factorize(const asm_desc *ds, const asm_problem *p, HostFactors &hf, 
                 for (int m = 0; m < M; ++m) U[(size_t)j * M + m] = tall ? Uh[m + (size_t)j * M] : VTh[j + (size_t)m * M];
             }
         }
-        // sign: the largest |component| of every V_j is positive (lowest index on ties)
-        const double thr = (np > 0 ? d[0] : 0.0) * (double)std::max(M, n) * 0x1p-52;
+        // sign: the largest |component| of every V_j is positive (lowest index on ties).
+        // Zero modes (flat on their interval): d <= d_1 max(M,n) 2^-52, and d up to
+        // d_1 max(M,n) 2^-40 when V_j changes sign -- there U_j = K~ V_j / d_j is not
+        // resolvable in FP64 (error ~ 2^-52 d_1 / d_j) while the likelihood is flat to
+        // exp(-(d Delta)^2 / 2) over the positivity interval Delta.
+        const double dmax = (double)std::max(M, n);
+        const double thr0 = (np > 0 ? d[0] : 0.0) * dmax * 0x1p-52, thr = (np > 0 ? d[0] : 0.0) * dmax * 0x1p-40;
         for (int j = 0; j < n; ++j) {
             double *v = &V[(size_t)j * n];
             int imax = 0;
@@ -628,9 +633,18 @@ int device_factorize(const asm_desc *ds, const asm_problem *p, HostFactors &hf, 
                 if (j < np)
                     for (int m = 0; m < M; ++m) U[(size_t)j * M + m] = -U[(size_t)j * M + m];
             }
-            if (j < np && !(d[j] > thr)) {
-                d[j] = 0.0;
-                for (int m = 0; m < M; ++m) U[(size_t)j * M + m] = 0.0;
+            if (j < np && d[j] <= thr) {
+                const double vm = std::fabs(v[imax]);
+                bool pos = false, neg = false;
+                for (int i = 0; i < n; ++i) {
+                    if (std::fabs(v[i]) < 0x1p-40 * vm) continue;
+                    pos = pos || v[i] > 0.0;
+                    neg = neg || v[i] < 0.0;
+                }
+                if (d[j] <= thr0 || (pos && neg)) {
+                    d[j] = 0.0;
+                    for (int m = 0; m < M; ++m) U[(size_t)j * M + m] = 0.0;
+                }
             }
         }
     }

@@ -48,8 +48,10 @@ def test_block_factors_reconstruct_whitened_kernel():
         Kb = dec.Kt[:, s:s + n]
         assert np.allclose(V.T @ V, np.eye(n), atol=1e-12)
         rec = U @ np.diag(d[:npr]) @ V[:, :npr].T
-        assert np.abs(rec - Kb).max() <= 1e-10 * np.abs(Kb).max()
         sv = np.linalg.svd(Kb, compute_uv=False)
+        # modes at or below d_1 max(M, n) 2^-40 may be flat (R2): the reconstruction misses
+        # at most sqrt(n) such singular values
+        assert np.abs(rec - Kb).max() <= 1e-10 * np.abs(Kb).max() + np.sqrt(n) * max(p.M, n) * 2.0 ** -40 * sv[0]
         keep = d[:npr] > 0
         assert np.allclose(d[:npr][keep], sv[:npr][keep], rtol=1e-8, atol=1e-12 * sv[0])
 
