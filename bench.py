@@ -15,7 +15,8 @@ are reported beside it, and, as side measurements outside the timed region,
 the batching workload (256 uneven problems in one handle), the grid-size
 sweep (N_omega 250..2000, 8192 chains), each in both paths, and ESS/s of the
 blocked-modes problem under four partition schemes (modes, components, the
-workload's two levels, the full hierarchy).
+workload's two levels, the full hierarchy), and the paper's own test case
+(optical conductivity on Matsubara data) on its uniform and non-uniform grids.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -63,6 +64,8 @@ def _args():
                     help="sweeps of the batching side measurement (0: skip)")
     ap.add_argument("--grid-sweeps", type=int, default=64,
                     help="sweeps per N_omega of the grid-size side measurement (0: skip)")
+    ap.add_argument("--paper-sweeps", type=int, default=5000,
+                    help="sweeps per grid of the paper-test-case side measurement (0: skip)")
     ap.add_argument("--hierarchy-sweeps", type=int, default=3000,
                     help="sweeps per partition scheme of the hierarchy side measurement (0: skip)")
     return ap.parse_args()
@@ -290,6 +293,36 @@ def hierarchy_side(args, asm, torch, stream):
     return out
 
 
+def paper_side(args, asm, torch, stream):
+    """The paper's own test case (optical conductivity model 2, accurate data,
+    60 bosonic Matsubara frequencies, beta = 15) over the full partition
+    hierarchy: uniform grids d_omega = 0.25 with N = 32, 64, 128, 256 (cutoff 8 ...
+    64) and the Gaussian, exponential and Lorentzian grids of N = 64.  Mixed
+    path, 1024 chains; updates/s, binned ESS/s, the seconds to an ESS of 1000
+    at every grid point (burn-in included), and the largest <sigma(omega)> beyond
+    omega = 8, where the spectrum is essentially zero (the paper finds spurious
+    peaks there as the uniform grid's cutoff grows)."""
+    cases = [("uniform", n) for n in (32, 64, 128, 256)] + [(g, 64) for g in ("gaussian", "exponential", "lorentzian")]
+    chains, burn, sweeps = 1024, 500, args.paper_sweeps
+    rows = []
+    for grid, N in cases:
+        p = W.paper_problem(2, 1e-3, grid, N)
+        gp = asm.Problem(p.K, p.G, p.C, asm.partition_hierarchy(N), w=p.w)
+        gp.sample(chains, 0, 1, 41)
+        t = _timed(torch, stream, lambda: gp.sample(chains, burn, sweeps, 42))
+        e = gp.mc_error()
+        a = gp.average()
+        ess = float(np.nanmin(e["ess"]))
+        tail = p.omega > 8.0
+        rows.append({"grid": grid, "N": N, "omega_max": float(p.omega[-1] + 0.5 * p.w[-1]),
+                     "updates_per_s": chains * (burn + sweeps) * N / t, "seconds": t, "ess_min": ess,
+                     "seconds_to_ess_1000": t * 1000.0 / ess if ess > 0 else None,
+                     "max_sigma_beyond_8": float(a["mean_A"][tail].max()) if tail.any() else None})
+        del gp
+    return {"workload": "optical_conductivity_model2_noise1e-3_beta15_60matsubara_hierarchy", "chains": chains,
+            "burn_in": burn, "sweeps": sweeps, "rows": rows}
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle is the reference arm for this method."""
     ws, rank, _ = _dist()
@@ -434,6 +467,7 @@ def main():
     batch = batch_side(args, asm, torch, stream) if (args.batch_sweeps > 0 and rank == 0) else None
     grid = grid_side(args, asm, torch, stream) if (args.grid_sweeps > 0 and rank == 0) else None
     hier = hierarchy_side(args, asm, torch, stream) if (args.hierarchy_sweeps > 0 and rank == 0) else None
+    paper = paper_side(args, asm, torch, stream) if (args.paper_sweeps > 0 and rank == 0) else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -461,6 +495,7 @@ def main():
             "batch": batch,
             "grid_sweep": grid,
             "partition_schemes": hier,
+            "paper_test_case": paper,
             "gpu_launches": int(sweep_launches + other_launches + args.steps),
             "clocks": clocks,
         }

@@ -635,7 +635,7 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
         // level of this sweep: same for every chain of the problem (Sec. IV.C)
         const int level = level_of_sweep(s, p.seed, p.problem_id, p.n_levels);
         const bool keep = s >= rg.burn_in;
-        long long win = -1;  // first move index of the window whose uniforms are in usm
+        int win = 0, win_end = -1;  // window [win, win_end) of moves whose uniforms are in usm
         const int nb = p.level_nblocks[level];
         const BlockDesc *bd = p.blocks + p.level_first[level];
 
@@ -679,8 +679,9 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                 // uniforms of a window come from one Philox call per lane (lane sl: ctr
                 // win/4 + sl, moves win + 4 sl + 0..3)
                 const int t = B.start + j;
-                if (win < 0 || t >= win + 4 * S) {
-                    win = (long long)(t / (4 * S)) * (4 * S);
+                if (t >= win_end) {
+                    win = (t / (4 * S)) * (4 * S);
+                    win_end = win + 4 * S;
                     unsigned long long c0 = (unsigned long long)(win >> 2) + (unsigned long long)sl;
                     unsigned long long c1 = (unsigned long long)s, c2 = (unsigned long long)q + p.chain_offset,
                                        c3 = p.problem_id;
@@ -692,12 +693,15 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     usm[4 * sl + 3] = uniform_from<T>(c3);
                     __syncwarp();
                 }
-                const T u = usm[t - (int)win];
-                // this move's record
-                const bool ok = mbar_wait_ready(full + rp.slot, rp.phase, kWaitLimit);
-                if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
-                    failed = true;
-                    break;
+                const T u = usm[t - win];
+                // this move's record: usually landed long ago (one test, one vote)
+                bool ok = mbar_test_wait(full + rp.slot, rp.phase);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    ok = ok || mbar_wait(full + rp.slot, rp.phase, kWaitLimit);
+                    if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
+                        failed = true;
+                        break;
+                    }
                 }
                 const T *st = reinterpret_cast<const T *>(stages + (size_t)rp.slot * sh.stage_bytes);
                 const T dj = st[2 * B.rs], ij = st[2 * B.rs + 1];
@@ -707,20 +711,17 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
 
                 T lo, hi;
                 team_bounds(lk, hk, lo, hi, S, team_base);
-                T delta;
-                if (!(hi > lo)) {
-                    delta = T(0);
-                    ++n_deg;
-                } else if (dj == T(0)) {
-                    delta = m_fma(u, hi - lo, lo);
-                    ++n_zero;
-                } else {
-                    delta = tn_step<T>(cj, dj, ij, lo, hi, u, capped);
-                }
-                if (!isfinite(delta)) {
-                    delta = T(0);
-                    ++n_bad;
-                }
+                // degenerate interval: no move; zero mode: flat on [lo, hi]; else the
+                // truncated Gaussian (the only branch)
+                const bool open = hi > lo;
+                T delta = m_fma(u, hi - lo, lo);
+                if (open && dj != T(0)) delta = tn_step<T>(cj, dj, ij, lo, hi, u, capped);
+                n_deg += open ? 0u : 1u;
+                n_zero += (open && dj == T(0)) ? 1u : 0u;
+                delta = open ? delta : T(0);
+                const bool fin = isfinite(delta);
+                n_bad += fin ? 0u : 1u;
+                delta = fin ? delta : T(0);
                 fused_pass_smem<T, KV>(f, delta, v0, r0, st, st + B.rs, kcnt, sl, S, lk, hk);
                 if (j < B.np && sl == 0) wsm[j] = dj * delta;
                 // release the record to the producer (one arrival per warp)

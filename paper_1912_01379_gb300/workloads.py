@@ -261,6 +261,91 @@ def grid_sweep_problem(N: int, density: str = "uniform", seed: int = 1005, chain
 
 
 # --------------------------------------------------------------------------
+# the paper's own test case (Sec. III): optical conductivity on bosonic
+# Matsubara frequencies
+# --------------------------------------------------------------------------
+
+def optical_conductivity(omega, model: int = 2):
+    """sigma(omega) of the paper's test models (Eq. model): a cutoff factor
+    1/(1 + (omega/4)^6) times a Drude peak (weight 0.3, width 0.3 for model 1,
+    0.6 for model 2) and two Lorentzians of weight 0.2 and width 1.2 at +-3."""
+    omega = np.asarray(omega, dtype=np.float64)
+    g0 = 0.3 if model == 1 else 0.6
+    peaks = 0.3 / (1.0 + (omega / g0) ** 2)
+    for sgn in (1.0, -1.0):
+        peaks = peaks + 0.2 / (1.0 + ((omega + sgn * 3.0) / 1.2) ** 2)
+    return peaks / (1.0 + (omega / 4.0) ** 6)
+
+
+def matsubara_kernel(omega_m, omega):
+    """K(i omega_m, omega) = (2/pi) omega^2 / (omega_m^2 + omega^2) (Eq. optcond) on omega > 0."""
+    om = np.asarray(omega_m, dtype=np.float64)[:, None]
+    w = np.asarray(omega, dtype=np.float64)[None, :]
+    return (2.0 / math.pi) * w * w / (om * om + w * w)
+
+
+def matsubara_data(omega_m, model: int = 2):
+    """Pi(i omega_m) = (2/pi) int_0^inf omega^2/(omega_m^2 + omega^2) sigma(omega) d omega by
+    adaptive quadrature (the integrand is smooth; tolerance 1e-13)."""
+    from scipy import integrate
+    out = np.empty(len(omega_m))
+    for i, om in enumerate(omega_m):
+        f = lambda x, om=om: (2.0 / math.pi) * x * x / (om * om + x * x) * optical_conductivity(x, model)
+        v = 0.0
+        for a, b in ((0.0, 2.0), (2.0, 6.0), (6.0, 20.0), (20.0, np.inf)):
+            v += integrate.quad(f, a, b, epsabs=1e-14, epsrel=1e-13, limit=400)[0]
+        out[i] = v
+    return out
+
+
+def half_line_grid(kind: str, N: int, param: float):
+    """Grids on [0, inf) from a density rho (Sec. V.B table): x_n = x(z_n), z_n = (n-1/2)/N,
+    weights w_n = (1/N) dx/dz.  kind: 'gaussian' (alpha), 'exponential' (beta),
+    'lorentzian' (gamma)."""
+    z = (np.arange(N) + 0.5) / N
+    if kind == "gaussian":
+        e = special.erfinv(z)
+        x = math.sqrt(2.0) * param * e
+        dxdz = math.sqrt(2.0 * math.pi) * param / 2.0 / np.exp(-e * e)
+    elif kind == "exponential":
+        x = -param * np.log1p(-z)
+        dxdz = param / (1.0 - z)
+    elif kind == "lorentzian":
+        x = param * np.tan(math.pi * z / 2.0)
+        dxdz = math.pi * param / 2.0 / np.cos(math.pi * z / 2.0) ** 2
+    else:
+        raise ValueError(kind)
+    return x, dxdz / N
+
+
+def paper_problem(model: int = 2, noise: float = 1e-3, grid: str = "uniform", N: int = 64,
+                  d_omega: float = 0.25, seed: int = 1006, chains: int = 1024) -> Problem:
+    """The paper's test case: optical conductivity model 1 or 2 continued from
+    Pi(i omega_m) (1 + r_m) on the first 60 bosonic Matsubara frequencies at
+    beta = 15, relative noise r_m of standard deviation `noise` (reading of the
+    paper's sigma_Pi), on a uniform grid omega_n = (n - 1/2) d_omega or a
+    Gaussian (alpha = 4), exponential (beta = 3) or Lorentzian (gamma = 2.5)
+    grid of N points.  Levels: the whole grid only (callers add blocks)."""
+    kinds = {"uniform": 0, "gaussian": 1, "exponential": 2, "lorentzian": 3}
+    rng = np.random.Generator(np.random.PCG64(seed + 7 * N + 1000 * kinds[grid] + 100000 * model))
+    beta, M = 15.0, 60
+    om = 2.0 * math.pi * np.arange(M) / beta
+    if grid == "uniform":
+        omega = (np.arange(N) + 0.5) * d_omega
+        w = np.full(N, d_omega)
+    else:
+        omega, w = half_line_grid(grid, N, {"gaussian": 4.0, "exponential": 3.0, "lorentzian": 2.5}[grid])
+    K = matsubara_kernel(om, omega)
+    pi_m = matsubara_data(om, model)
+    G = pi_m * (1.0 + noise * rng.standard_normal(M))
+    C = np.diag((noise * pi_m) ** 2)
+    fbar = optical_conductivity(omega, model) * w
+    return Problem(f"paper_model{model}_{grid}_N{N}", K, G, C, omega, w, [np.array([0], np.int32)], fbar,
+                   chains=chains, burn_in=500, sweeps=5000,
+                   extra={"beta": beta, "omega_m": om, "pi_exact": pi_m, "noise": noise, "model": model})
+
+
+# --------------------------------------------------------------------------
 # small cases for tests
 # --------------------------------------------------------------------------
 
