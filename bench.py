@@ -302,11 +302,17 @@ def paper_side(args, asm, torch, stream):
     at every grid point (burn-in included), and the largest <sigma(omega)> beyond
     omega = 8, where the spectrum is essentially zero (the paper finds spurious
     peaks there as the uniform grid's cutoff grows)."""
-    cases = [("uniform", n) for n in (32, 64, 128, 256)] + [(g, 64) for g in ("gaussian", "exponential", "lorentzian")]
+    from paper_1912_01379_gb300 import default_model
+    cases = [("uniform", n, None) for n in (32, 64, 128, 256)] + [(g, 64, None) for g in
+                                                                 ("gaussian", "exponential", "lorentzian")]
+    # the Gaussian grid whose default model fits the data best (Sec. VI)
+    p0 = W.paper_problem(2, 1e-3, "gaussian", 64)
+    alpha, _ = default_model.fit_grid_density("gaussian", p0.extra["omega_m"], p0.G)
+    cases.append(("gaussian", 64, alpha))
     chains, burn, sweeps = 1024, 500, args.paper_sweeps
     rows = []
-    for grid, N in cases:
-        p = W.paper_problem(2, 1e-3, grid, N)
+    for grid, N, param in cases:
+        p = W.paper_problem(2, 1e-3, grid, N, grid_param=param)
         gp = asm.Problem(p.K, p.G, p.C, asm.partition_hierarchy(N), w=p.w)
         gp.sample(chains, 0, 1, 41)
         t = _timed(torch, stream, lambda: gp.sample(chains, burn, sweeps, 42))
@@ -314,7 +320,7 @@ def paper_side(args, asm, torch, stream):
         a = gp.average()
         ess = float(np.nanmin(e["ess"]))
         tail = p.omega > 8.0
-        rows.append({"grid": grid, "N": N, "omega_max": float(p.omega[-1] + 0.5 * p.w[-1]),
+        rows.append({"grid": grid, "N": N, "grid_param": param, "omega_max": float(p.omega[-1] + 0.5 * p.w[-1]),
                      "updates_per_s": chains * (burn + sweeps) * N / t, "seconds": t, "ess_min": ess,
                      "seconds_to_ess_1000": t * 1000.0 / ess if ess > 0 else None,
                      "max_sigma_beyond_8": float(a["mean_A"][tail].max()) if tail.any() else None})

@@ -319,13 +319,14 @@ def half_line_grid(kind: str, N: int, param: float):
 
 
 def paper_problem(model: int = 2, noise: float = 1e-3, grid: str = "uniform", N: int = 64,
-                  d_omega: float = 0.25, seed: int = 1006, chains: int = 1024) -> Problem:
+                  d_omega: float = 0.25, seed: int = 1006, chains: int = 1024, grid_param=None) -> Problem:
     """The paper's test case: optical conductivity model 1 or 2 continued from
     Pi(i omega_m) (1 + r_m) on the first 60 bosonic Matsubara frequencies at
     beta = 15, relative noise r_m of standard deviation `noise` (reading of the
     paper's sigma_Pi), on a uniform grid omega_n = (n - 1/2) d_omega or a
     Gaussian (alpha = 4), exponential (beta = 3) or Lorentzian (gamma = 2.5)
-    grid of N points.  Levels: the whole grid only (callers add blocks)."""
+    grid of N points (grid_param overrides alpha, beta or gamma).  Levels: the
+    whole grid only (callers add blocks)."""
     kinds = {"uniform": 0, "gaussian": 1, "exponential": 2, "lorentzian": 3}
     rng = np.random.Generator(np.random.PCG64(seed + 7 * N + 1000 * kinds[grid] + 100000 * model))
     beta, M = 15.0, 60
@@ -334,7 +335,8 @@ def paper_problem(model: int = 2, noise: float = 1e-3, grid: str = "uniform", N:
         omega = (np.arange(N) + 0.5) * d_omega
         w = np.full(N, d_omega)
     else:
-        omega, w = half_line_grid(grid, N, {"gaussian": 4.0, "exponential": 3.0, "lorentzian": 2.5}[grid])
+        param = grid_param if grid_param is not None else {"gaussian": 4.0, "exponential": 3.0, "lorentzian": 2.5}[grid]
+        omega, w = half_line_grid(grid, N, param)
     K = matsubara_kernel(om, omega)
     pi_m = matsubara_data(om, model)
     G = pi_m * (1.0 + noise * rng.standard_normal(M))
