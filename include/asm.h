@@ -95,6 +95,14 @@ typedef struct {
     int P;                      /* number of grid-density parameters theta (0: none) */
     const double *dK_dtheta;    /* P x M x N: dK/dtheta_p (row-major per p), or NULL */
     const double *dw_dtheta;    /* P x N: dw/dtheta_p, or NULL */
+    /* Gamma prior prod_n fbar_n^(a_n - 1) (Eq. compat, Sec. V.C: sampling on this
+     * grid what flat sampling on another grid gives; a_n = N rho(x_n) / (N' rho'(x_n))),
+     * N values a_n >= 1, or NULL (flat).  Every move's draw from the fit's 1-D
+     * conditional is then a proposal accepted with probability min(1, prior ratio)
+     * (a Metropolis-Hastings step inside the Gibbs move, second uniform: word t mod 4
+     * of ctr {t/4, s, q, problem xor 2^63}).  a_n < 1 is rejected (ASM_ERR_ARG): its
+     * density diverges at 0 where clamped moves leave exact zeros. */
+    const double *prior_shape;
 } asm_desc;
 
 /* Counters of the last asm_sample run (asm_status). */
@@ -118,6 +126,7 @@ typedef struct {
     int32_t work_items;         /* (problem, chain group) items of the last sweep launch */
     int32_t min_blocks;         /* CTAs per SM the last sweep launch's registers were budgeted for (1, 2) */
     int32_t reserved_;
+    int64_t prior_rejections;   /* moves whose proposal the gamma prior rejected */
 } asm_stats;
 
 /* Set-up (Sec. IV: whitening C^{-1} = T^T T by Cholesky, K~ = T K, g~ = T G;

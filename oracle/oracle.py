@@ -71,6 +71,8 @@ def lib():
                                   ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_int, _dp, _dp, _dp, _dp, _dp,
                                   ct.c_int, _lp]
         L.ora_run_ids.restype = ct.c_int
+        L.ora_set_prior.argtypes = [ct.c_void_p, _dp]
+        L.ora_set_prior.restype = ct.c_int
         _lib = L
     return _lib
 
@@ -142,7 +144,7 @@ class Decomposition:
 class OracleProblem:
     ERRORS = {-1: "shape", -2: "not SPD", -3: "non-finite", -4: "improper zero mode"}
 
-    def __init__(self, K, G, C, levels):
+    def __init__(self, K, G, C, levels, prior_shape=None):
         K = np.ascontiguousarray(K, dtype=np.float64)
         G = np.ascontiguousarray(G, dtype=np.float64)
         C = np.ascontiguousarray(C, dtype=np.float64)
@@ -156,6 +158,10 @@ class OracleProblem:
         if not self._h:
             raise ValueError(f"oracle setup failed: {self.ERRORS.get(err.value, err.value)}")
         self.err = err.value
+        if prior_shape is not None:
+            a = np.ascontiguousarray(prior_shape, dtype=np.float64)
+            if a.shape != (self.N,) or lib().ora_set_prior(self._h, _d(a)) != 0:
+                raise ValueError("prior shape must be N values >= 1")
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -34,7 +34,8 @@ class asm_desc(ct.Structure):
                 ("K", _dp), ("G", _dp), ("C", _dp), ("w", _dp),
                 ("n_levels", ct.c_int), ("level_nblocks", _ip), ("block_start", _ip),
                 ("Kt", _dp), ("gt", _dp), ("d", _dp), ("V", _dp), ("U", _dp),
-                ("flags", ct.c_uint32), ("P", ct.c_int), ("dK_dtheta", _dp), ("dw_dtheta", _dp)]
+                ("flags", ct.c_uint32), ("P", ct.c_int), ("dK_dtheta", _dp), ("dw_dtheta", _dp),
+                ("prior_shape", _dp)]
 
 
 class asm_stats(ct.Structure):
@@ -47,7 +48,7 @@ class asm_stats(ct.Structure):
                 ("timeouts", ct.c_int64), ("graph_replays", ct.c_int64), ("tc_refreshes", ct.c_int64),
                 ("team_lanes", ct.c_int32),
                 ("consumers_per_cta", ct.c_int32), ("ctas", ct.c_int32), ("work_items", ct.c_int32),
-                ("min_blocks", ct.c_int32), ("reserved_", ct.c_int32)]
+                ("min_blocks", ct.c_int32), ("reserved_", ct.c_int32), ("prior_rejections", ct.c_int64)]
 
 
 EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",
@@ -160,7 +161,7 @@ def _require_cuda():
     return torch
 
 
-def _make_desc(K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None):
+def _make_desc(K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None, prior_shape=None):
     """asm_desc of one problem plus the arrays it points into (kept alive by
     the caller until asm_setup returns)."""
     keep = []
@@ -191,6 +192,11 @@ def _make_desc(K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=
         assert dK.shape == (P, M, N) and dw.shape == (P, N)
         keep += [dK, dw]
         d.P, d.dK_dtheta, d.dw_dtheta = P, _dptr(dK), _dptr(dw)
+    if prior_shape is not None:
+        a = np.ascontiguousarray(prior_shape, dtype=np.float64)
+        assert a.shape == (N,)
+        keep.append(a)
+        d.prior_shape = _dptr(a)
     return d, keep, (M, N, w, levels, P)
 
 
@@ -309,10 +315,10 @@ class Problem(_Handle):
     weights (A = fbar / w).  `factors` (optional) is an object with Kt, gt, d,
     V, U arrays in the layout of asm_desc to use given singular vectors."""
 
-    def __init__(self, K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None):
+    def __init__(self, K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None, prior_shape=None):
         L = load()
         d, self._keep, (self.M, self.N, self.w, self.levels, self.P) = _make_desc(
-            K, G, C, levels, w, factors, dK_dtheta, dw_dtheta)
+            K, G, C, levels, w, factors, dK_dtheta, dw_dtheta, prior_shape)
         h = ct.c_void_p()
         _check(L.asm_setup(ct.byref(d), ct.byref(h)), "asm_setup")
         self._h = h

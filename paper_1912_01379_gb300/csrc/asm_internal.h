@@ -44,7 +44,8 @@ struct Counters {            // device counters, first bytes of the workspace
     unsigned long long degenerate, zero_mode, tail_capped, nonfinite;
     unsigned long long drift_bits;   // max relative chi2 drift, as ordered bits of a double
     unsigned long long timeouts;     // bounded waits that gave up (the launch then stopped early)
-    unsigned long long pad[2];
+    unsigned long long prior_rejections;   // proposals the gamma prior rejected
+    unsigned long long pad;
 };
 
 template <class T>
@@ -75,6 +76,8 @@ struct SweepParams {
     // the tensor-core refresh of the mixed path
     const float *Khi, *Klo;
     int ldK;
+    // gamma prior: a_n - 1 per grid point (nullptr: flat)
+    const T *prior_am1;
 };
 
 // What every problem of one launch shares: the CTA shape and the
@@ -92,6 +95,7 @@ struct LaunchShape {
     int mpad;                         // shared-memory stride of the residual (>= max M)
     int n_items;                      // (problem, chain group) work items
     int minb;                         // register budget: 1 or 2 CTAs per SM
+    int prior;                        // 1: kernels with the gamma prior's acceptance step
 };
 
 // Per-launch control block in device memory: the work queue and the launch's
@@ -124,6 +128,8 @@ ASM_DECLARE_SWEEP_LAUNCHER(float, f32_m1)
 ASM_DECLARE_SWEEP_LAUNCHER(float, f32_m2)
 ASM_DECLARE_SWEEP_LAUNCHER(double, f64_m1)
 ASM_DECLARE_SWEEP_LAUNCHER(double, f64_m2)
+ASM_DECLARE_SWEEP_LAUNCHER(float, f32_prior)     // with the gamma prior, one CTA per SM
+ASM_DECLARE_SWEEP_LAUNCHER(double, f64_prior)
 #undef ASM_DECLARE_SWEEP_LAUNCHER
 // Tensor-core residual refresh of the mixed path (asm_refresh_tc.cu): grid of
 // (chain tiles of 128) x n_problems CTAs; max_bn = the largest refresh_tc_bn(M).

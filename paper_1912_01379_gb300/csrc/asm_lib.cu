@@ -351,6 +351,7 @@ struct WsLayout {
 struct PrecBuffers {
     void *V = nullptr, *R = nullptr, *d = nullptr, *invd = nullptr, *meta = nullptr,
          *rec = nullptr, *Ut = nullptr, *Um = nullptr;
+    void *prior_am1 = nullptr;   // a_n - 1 of the gamma prior (nullptr: flat)
 };
 
 struct asm_problem {
@@ -510,7 +511,7 @@ int upload(void **dst, const std::vector<T> &src)
 
 void free_prec(PrecBuffers &b)
 {
-    void *ptrs[] = {b.V, b.R, b.d, b.invd, b.meta, b.rec, b.Ut, b.Um};
+    void *ptrs[] = {b.V, b.R, b.d, b.invd, b.meta, b.rec, b.Ut, b.Um, b.prior_am1};
     for (void *x : ptrs)
         if (x) cudaFree(x);
     b = PrecBuffers{};
@@ -843,6 +844,7 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.Khi = p->d_Khi;
     sp.Klo = p->d_Klo;
     sp.ldK = p->ldK;
+    sp.prior_am1 = (const T *)b.prior_am1;
     sp.gt = p->d_gt;
     sp.chi2 = (double *)(ws + L.chi2);
     sp.S1p = (double *)(ws + L.S1p);
@@ -855,7 +857,7 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
 }
 
 // Shared memory of the sweep kernel: per team c, w, r~ and the uniforms of a
-// window of 4S moves; the ring's `full`
+// window of 4S moves (draws and prior acceptances); the ring's `full`
 // and `empty` barriers and `depth` record stages.  Consumer warps per CTA:
 // enough that the CTAs about cover the SMs once (all chains of an SM then
 // share one ring), or the tuned count.  CTAs per SM: as many as the work
@@ -865,15 +867,18 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
 int ctas_per_sm(int precision, const LaunchShape &sh, int kv, bool batch)
 {
     if (precision == ASM_FP64)
-        return sh.minb == 2 ? sweep_ctas_per_sm_f64_m2(sh, kv, batch) : sweep_ctas_per_sm_f64_m1(sh, kv, batch);
-    return sh.minb == 2 ? sweep_ctas_per_sm_f32_m2(sh, kv, batch) : sweep_ctas_per_sm_f32_m1(sh, kv, batch);
+        return sh.prior ? sweep_ctas_per_sm_f64_prior(sh, kv, batch)
+               : sh.minb == 2 ? sweep_ctas_per_sm_f64_m2(sh, kv, batch) : sweep_ctas_per_sm_f64_m1(sh, kv, batch);
+    return sh.prior ? sweep_ctas_per_sm_f32_prior(sh, kv, batch)
+           : sh.minb == 2 ? sweep_ctas_per_sm_f32_m2(sh, kv, batch) : sweep_ctas_per_sm_f32_m1(sh, kv, batch);
 }
 
 template <class T>
 bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long long total_warps, int kv,
-                bool batch, int want_consumers, int minb)
+                bool batch, int want_consumers, int minb, bool prior)
 {
-    sh.minb = minb;
+    sh.minb = prior ? 1 : minb;   // the prior's kernels exist for one CTA per SM
+    sh.prior = prior ? 1 : 0;
     constexpr int kSMs = 152;
     const int TW = 32 / S;
     const int prec = sizeof(T) == 8 ? ASM_FP64 : ASM_MIXED;
@@ -890,7 +895,7 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
     }
     sh.stage_bytes = (int)align_up((size_t)max_rec * sizeof(T), 128);
     auto fixed = [&](int c) {
-        return align_up((size_t)c * TW * (2 * sh.cpad + sh.mpad + 4 * S) * sizeof(T), 128) + 256;
+        return align_up((size_t)c * TW * (2 * sh.cpad + sh.mpad + 8 * S) * sizeof(T), 128) + 256;
     };
     int max_depth = 16;
     if (const char *e = std::getenv("ASM_RING_DEPTH")) {            // tuning override
@@ -912,7 +917,7 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
             if (fixed(consumers) + (size_t)depth * sh.stage_bytes > 227 * 1024) return false;
             sh.consumers = consumers;
             sh.depth = depth;
-            sh.off_full = (int)align_up((size_t)consumers * TW * (2 * sh.cpad + sh.mpad + 4 * S) * sizeof(T), 128);
+            sh.off_full = (int)align_up((size_t)consumers * TW * (2 * sh.cpad + sh.mpad + 8 * S) * sizeof(T), 128);
             sh.off_empty = sh.off_full + 128;
             sh.off_stages = sh.off_full + 256;
             return true;
@@ -1056,8 +1061,10 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
     // state would spill
     int minb = total_warps > 152LL * kMaxConsumers && !(sizeof(T) == 8 && kv >= 16) ? 2 : 1;
     if (h->tuned_minb) minb = h->tuned_minb;
+    bool prior = false;   // any problem with a gamma prior: the kernels with the acceptance step
+    for (asm_problem *u : us) prior = prior || (sizeof(T) == 8 ? u->b64.prior_am1 : u->b32.prior_am1) != nullptr;
     LaunchShape sh{};
-    if (!plan_shape<T>(sh, S, max_rec, max_np, max_M, total_warps, kv, batch, h->tuned_consumers, minb))
+    if (!plan_shape<T>(sh, S, max_rec, max_np, max_M, total_warps, kv, batch, h->tuned_consumers, minb, prior))
         return ASM_ERR_TOO_LARGE;
     // work items, the costliest problems first (a longest-first queue)
     std::vector<int> order(us.size());
@@ -1097,11 +1104,13 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
     const SweepParams<T> &p0 = probs[0];   // a single problem's parameters travel by value
     auto sweep = [&](cudaStream_t st) {
         if constexpr (sizeof(T) == 8)
-            return sh.minb == 2 ? launch_sweeps_f64_m2(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st)
-                                : launch_sweeps_f64_m1(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
+            return sh.prior ? launch_sweeps_f64_prior(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st)
+                   : sh.minb == 2 ? launch_sweeps_f64_m2(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st)
+                                  : launch_sweeps_f64_m1(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
         else
-            return sh.minb == 2 ? launch_sweeps_f32_m2(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st)
-                                : launch_sweeps_f32_m1(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
+            return sh.prior ? launch_sweeps_f32_prior(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st)
+                   : sh.minb == 2 ? launch_sweeps_f32_m2(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st)
+                                  : launch_sweeps_f32_m1(p0, d_probs, d_items, ctrl, sh, kv, batch, ctas, st);
     };
     auto binning = [&](cudaStream_t st) {
         bin_kernel<T><<<n_refresh, 128, 0, st>>>(d_probs, chains, ctrl);
@@ -1136,7 +1145,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             key.consumers = sh.consumers;
             key.depth = sh.depth;
             key.n_items = sh.n_items;
-            key.minb = sh.minb;
+            key.minb = sh.minb + 4 * sh.prior;
             key.refresh_smem = tc ? refresh_tc_smem(max_bn) + 1 : rsmem;
             key.seed = p0.seed;   // by value in a single problem's launch
             key.problem_id = p0.problem_id;
@@ -1348,6 +1357,21 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
         delete p;
         return ASM_ERR_NONFINITE;
     }
+    // gamma prior (Eq. compat): shapes a_n >= 1; all 1 is the flat measure
+    std::vector<double> prior_am1;
+    if (ds->prior_shape) {
+        bool any = false;
+        for (int n = 0; n < N; ++n) {
+            const double a = ds->prior_shape[n];
+            if (!std::isfinite(a)) { delete p; return ASM_ERR_NONFINITE; }
+            if (!(a >= 1.0)) { delete p; return ASM_ERR_ARG; }
+            any = any || a != 1.0;
+        }
+        if (any) {
+            prior_am1.resize(N);
+            for (int n = 0; n < N; ++n) prior_am1[n] = ds->prior_shape[n] - 1.0;
+        }
+    }
     HostFactors hf;
     int rc = ASM_OK;
     if (given) {
@@ -1431,6 +1455,13 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
         (rc = build_precision<float>(p, hf, p->b32))) {
         asm_destroy(p);
         return rc;
+    }
+    if (!prior_am1.empty()) {
+        std::vector<float> am32(prior_am1.begin(), prior_am1.end());
+        if ((rc = upload(&p->b64.prior_am1, prior_am1)) || (rc = upload(&p->b32.prior_am1, am32))) {
+            asm_destroy(p);
+            return rc;
+        }
     }
     // K~ in TF32 high/low parts for the tensor-core refresh
     p->ldK = round_up_int(N, kRefreshTcLdK);
@@ -1569,6 +1600,7 @@ int read_counters_all(asm_problem *p, Counters *c)
         c->tail_capped += cu.tail_capped;
         c->nonfinite += cu.nonfinite;
         c->timeouts += cu.timeouts;
+        c->prior_rejections += cu.prior_rejections;
         c->drift_bits = std::max(c->drift_bits, cu.drift_bits);   // non-negative doubles order like their bits
     }
     return ASM_OK;
@@ -1921,6 +1953,7 @@ int asm_status(asm_problem *p, asm_stats *out)
     out->timed_launches = p->timed_launches;
     out->sweep_kernel_ms = p->timed_ms;
     out->timeouts = (int64_t)c.timeouts;
+    out->prior_rejections = (int64_t)c.prior_rejections;
     out->graph_replays = p->graph_replays;
     out->tc_refreshes = p->tc_refreshes;
     out->team_lanes = p->last_team;

@@ -593,7 +593,7 @@ __device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchSha
 // A consumer warp: its team(s) of S lanes run the chains of chain group
 // `group` (consumers x 32/S chains) of problem p for the launch's sweeps.
 // --------------------------------------------------------------------------
-template <class T, int KV>
+template <class T, int KV, bool PRIOR>
 __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchShape &sh, const SweepRange &rg,
                                         int group, unsigned char *smem_raw, unsigned long long *full,
                                         unsigned long long *empty, unsigned char *stages, RingPos &rp,
@@ -616,10 +616,10 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
 
     // per team in shared memory: c (cpad), w (cpad), r~ (mpad) and the uniforms of the
     // current window of 4S moves
-    T *csm = reinterpret_cast<T *>(smem_raw) + (size_t)(wcta * TW + team) * (2 * sh.cpad + sh.mpad + 4 * S);
+    T *csm = reinterpret_cast<T *>(smem_raw) + (size_t)(wcta * TW + team) * (2 * sh.cpad + sh.mpad + 8 * S);
     T *wsm = csm + sh.cpad;
     T *rsm = wsm + sh.cpad;
-    T *usm = rsm + sh.mpad;
+    T *usm = rsm + sh.mpad;   // 4S uniforms of the draws, then 4S of the prior's acceptances
     T *Rq = p.R + (size_t)q * p.ldR;
     for (int m = sl; m < p.M; m += S) rsm[m] = Rq[m];
     T *Fq = p.F + (size_t)q * p.ldF;
@@ -628,7 +628,7 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
     __syncwarp();
 
     T f[KV][VEC];
-    unsigned n_deg = 0, n_zero = 0, n_bad = 0;   // per launch: at most 64 sweeps of moves
+    unsigned n_deg = 0, n_zero = 0, n_bad = 0, n_rej = 0;   // per launch: at most 64 sweeps of moves
     int capped = 0;
     const long long s_end = rg.sweep0 + rg.nsweeps;
     for (long long s = rg.sweep0; s < s_end && !failed; ++s) {
@@ -691,6 +691,17 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     usm[4 * sl + 1] = uniform_from<T>(c1);
                     usm[4 * sl + 2] = uniform_from<T>(c2);
                     usm[4 * sl + 3] = uniform_from<T>(c3);
+                    if constexpr (PRIOR) {   // acceptance uniforms: ctr {t/4, s, q, problem xor 2^63}
+                        c0 = (unsigned long long)(win >> 2) + (unsigned long long)sl;
+                        c1 = (unsigned long long)s;
+                        c2 = (unsigned long long)q + p.chain_offset;
+                        c3 = p.problem_id ^ (1ull << 63);
+                        philox4x64_10(c0, c1, c2, c3, p.seed, 0ull);
+                        usm[4 * S + 4 * sl] = uniform_from<T>(c0);
+                        usm[4 * S + 4 * sl + 1] = uniform_from<T>(c1);
+                        usm[4 * S + 4 * sl + 2] = uniform_from<T>(c2);
+                        usm[4 * S + 4 * sl + 3] = uniform_from<T>(c3);
+                    }
                     __syncwarp();
                 }
                 const T u = usm[t - win];
@@ -722,6 +733,48 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                 const bool fin = isfinite(delta);
                 n_bad += fin ? 0u : 1u;
                 delta = fin ? delta : T(0);
+                if constexpr (PRIOR) if (delta != T(0)) {
+                    // gamma prior (Eq. compat): the draw is a proposal, accepted with
+                    // probability min(1, prod ((f + delta V)_+ / f)^(a - 1)) over the block
+                    T lsum = T(0);
+                    unsigned zflags = 0u;   // 1: a proposed value is 0, 2: a current value is 0
+#pragma unroll
+                    for (int k = 0; k < KV; ++k) {
+                        if (k < kcnt) {
+                            T vv[VEC];
+                            if (k == 0) {
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) vv[v] = v0[v];
+                            } else {
+                                lds_v(st + VEC * (k * S + sl), vv);
+                            }
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) {
+                                const int nl = VEC * (k * S + sl) + v;
+                                if (nl < B.n) {
+                                    const T am1 = __ldg(p.prior_am1 + B.start + nl);
+                                    if (am1 != T(0)) {
+                                        const T x0 = f[k][v];
+                                        const T x1 = m_max(m_fma(delta, vv[v], x0), T(0));
+                                        if (x1 == T(0)) zflags |= 1u;
+                                        else if (x0 == T(0)) zflags |= 2u;
+                                        else lsum += am1 * (m_log(x1) - m_log(x0));
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    for (int off = 1; off < S; off <<= 1) {
+                        lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+                        zflags |= __shfl_xor_sync(0xffffffffu, zflags, off);
+                    }
+                    const T lr = (zflags & 1u) ? -CUDART_INF_F : (zflags & 2u) ? CUDART_INF_F : lsum;
+                    const T ua = usm[4 * S + (t - win)];
+                    if (!(m_log(ua) < lr)) {
+                        delta = T(0);
+                        ++n_rej;
+                    }
+                }
                 fused_pass_smem<T, KV>(f, delta, v0, r0, st, st + B.rs, kcnt, sl, S, lk, hk);
                 if (j < B.np && sl == 0) wsm[j] = dj * delta;
                 // release the record to the producer (one arrival per warp)
@@ -777,6 +830,7 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
             if (n_deg) atomicAdd(&p.counters->degenerate, (unsigned long long)n_deg);
             if (n_zero) atomicAdd(&p.counters->zero_mode, (unsigned long long)n_zero);
             if (n_bad) atomicAdd(&p.counters->nonfinite, (unsigned long long)n_bad);
+            if (n_rej) atomicAdd(&p.counters->prior_rejections, (unsigned long long)n_rej);
             if (capped) atomicAdd(&p.counters->tail_capped, (unsigned long long)capped);
         }
     }
@@ -790,7 +844,7 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
 // grid constant p0.  Several: each item's parameters are copied from probs
 // into shared memory.
 // --------------------------------------------------------------------------
-template <class T, int KV, bool BATCH, int MINB>
+template <class T, int KV, bool BATCH, int MINB, bool PRIOR>
 __global__ void __launch_bounds__(32 * (kMaxConsumers + 1), MINB) sweep_kernel(const __grid_constant__ SweepParams<T> p0,
                                                     const SweepParams<T> *__restrict__ probs,
                                                     const WorkItem *__restrict__ items, RunCtrl *ctrl,
@@ -831,48 +885,48 @@ __global__ void __launch_bounds__(32 * (kMaxConsumers + 1), MINB) sweep_kernel(c
         if (wcta == shape.consumers)
             produce(p, shape, rg, full, empty, stages, rp, failed);
         else
-            consume<T, KV>(p, shape, rg, w.group, smem_raw, full, empty, stages, rp, failed);
+            consume<T, KV, PRIOR>(p, shape, rg, w.group, smem_raw, full, empty, stages, rp, failed);
         __syncthreads();   // the item is finished before sp and s_item change
     }
 }
 
-template <class T, int KV, bool BATCH, int MINB>
+template <class T, int KV, bool BATCH, int MINB, bool PRIOR>
 cudaError_t launch_sweep_kernel(const SweepParams<T> &p0, const SweepParams<T> *probs, const WorkItem *items,
                                 RunCtrl *ctrl, const LaunchShape &shape, int ctas, cudaStream_t stream)
 {
     const size_t smem = (size_t)shape.off_stages + (size_t)shape.depth * shape.stage_bytes;
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, KV, BATCH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, KV, BATCH, MINB, PRIOR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    sweep_kernel<T, KV, BATCH, MINB><<<(unsigned)ctas, 32 * (shape.consumers + 1), smem, stream>>>(p0, probs, items, ctrl,
+    sweep_kernel<T, KV, BATCH, MINB, PRIOR><<<(unsigned)ctas, 32 * (shape.consumers + 1), smem, stream>>>(p0, probs, items, ctrl,
                                                                                              shape);
     return cudaGetLastError();
 }
 
-template <class T, int KV, bool BATCH, int MINB>
+template <class T, int KV, bool BATCH, int MINB, bool PRIOR>
 int sweep_ctas_per_sm(const LaunchShape &shape)
 {
     const size_t smem = (size_t)shape.off_stages + (size_t)shape.depth * shape.stage_bytes;
-    if (cudaFuncSetAttribute(sweep_kernel<T, KV, BATCH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(sweep_kernel<T, KV, BATCH, MINB, PRIOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, KV, BATCH, MINB>, 32 * (shape.consumers + 1),
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, KV, BATCH, MINB, PRIOR>, 32 * (shape.consumers + 1),
                                                       smem) != cudaSuccess)
         return 0;
     return n;
 }
 
 // dispatch over the register tile (kv) and the batch flag, for one residency
-// MINB (CTAs per SM the registers are budgeted for)
-template <class T, int MINB, int... KVs>
+// MINB (CTAs per SM the registers are budgeted for) and prior flag
+template <class T, int MINB, bool PRIOR, int... KVs>
 struct SweepDispatch {
     static cudaError_t launch(const SweepParams<T> &p0, const SweepParams<T> *probs, const WorkItem *items,
                               RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch, int ctas, cudaStream_t s)
     {
         cudaError_t e = cudaErrorInvalidValue;
-        ((kv == KVs ? (e = batch ? launch_sweep_kernel<T, KVs, true, MINB>(p0, probs, items, ctrl, shape, ctas, s)
-                                 : launch_sweep_kernel<T, KVs, false, MINB>(p0, probs, items, ctrl, shape, ctas, s),
+        ((kv == KVs ? (e = batch ? launch_sweep_kernel<T, KVs, true, MINB, PRIOR>(p0, probs, items, ctrl, shape, ctas, s)
+                                 : launch_sweep_kernel<T, KVs, false, MINB, PRIOR>(p0, probs, items, ctrl, shape, ctas, s),
                        0)
                     : 0),
          ...);
@@ -881,8 +935,8 @@ struct SweepDispatch {
     static int per_sm(const LaunchShape &shape, int kv, bool batch)
     {
         int n = 0;
-        ((kv == KVs ? (n = batch ? sweep_ctas_per_sm<T, KVs, true, MINB>(shape)
-                                 : sweep_ctas_per_sm<T, KVs, false, MINB>(shape),
+        ((kv == KVs ? (n = batch ? sweep_ctas_per_sm<T, KVs, true, MINB, PRIOR>(shape)
+                                 : sweep_ctas_per_sm<T, KVs, false, MINB, PRIOR>(shape),
                        0)
                     : 0),
          ...);

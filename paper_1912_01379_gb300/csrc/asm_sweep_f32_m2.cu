@@ -1,13 +1,13 @@
-// FP32 chain state (the mixed-precision path): instantiations of the sweep kernel budgeted for 2 CTAs per SM
-// (at most 128 registers per thread).
+// FP32 chain state (the mixed-precision path): instantiations of the sweep kernel budgeted for 2 CTAs per SM (at most 128 registers per thread).
 #include "asm_sweep.cuh"
 
 namespace asmgb {
 
-using Dispatch = SweepDispatch<float, 2, 1, 2, 4, 8, 16>;
+using Dispatch = SweepDispatch<float, 2, false, 1, 2, 4, 8, 16>;
 
-cudaError_t launch_sweeps_f32_m2(const SweepParams<float> &p0, const SweepParams<float> *probs, const WorkItem *items,
-                                RunCtrl *ctrl, const LaunchShape &shape, int kv, bool batch, int ctas, cudaStream_t s)
+cudaError_t launch_sweeps_f32_m2(const SweepParams<float> &p0, const SweepParams<float> *probs,
+                                  const WorkItem *items, RunCtrl *ctrl, const LaunchShape &shape, int kv,
+                                  bool batch, int ctas, cudaStream_t s)
 {
     return Dispatch::launch(p0, probs, items, ctrl, shape, kv, batch, ctas, s);
 }

@@ -1,0 +1,20 @@
+// FP32 chain state (the mixed-precision path): instantiations of the sweep kernel with the gamma prior's acceptance step, budgeted for one CTA per SM.
+#include "asm_sweep.cuh"
+
+namespace asmgb {
+
+using Dispatch = SweepDispatch<float, 1, true, 1, 2, 4, 8, 16>;
+
+cudaError_t launch_sweeps_f32_prior(const SweepParams<float> &p0, const SweepParams<float> *probs,
+                                  const WorkItem *items, RunCtrl *ctrl, const LaunchShape &shape, int kv,
+                                  bool batch, int ctas, cudaStream_t s)
+{
+    return Dispatch::launch(p0, probs, items, ctrl, shape, kv, batch, ctas, s);
+}
+
+int sweep_ctas_per_sm_f32_prior(const LaunchShape &shape, int kv, bool batch)
+{
+    return Dispatch::per_sm(shape, kv, batch);
+}
+
+}  // namespace asmgb

@@ -1,0 +1,20 @@
+// FP64 chain state: instantiations of the sweep kernel with the gamma prior's acceptance step, budgeted for one CTA per SM.
+#include "asm_sweep.cuh"
+
+namespace asmgb {
+
+using Dispatch = SweepDispatch<double, 1, true, 1, 2, 4, 8, 16, 32>;
+
+cudaError_t launch_sweeps_f64_prior(const SweepParams<double> &p0, const SweepParams<double> *probs,
+                                  const WorkItem *items, RunCtrl *ctrl, const LaunchShape &shape, int kv,
+                                  bool batch, int ctas, cudaStream_t s)
+{
+    return Dispatch::launch(p0, probs, items, ctrl, shape, kv, batch, ctas, s);
+}
+
+int sweep_ctas_per_sm_f64_prior(const LaunchShape &shape, int kv, bool batch)
+{
+    return Dispatch::per_sm(shape, kv, batch);
+}
+
+}  // namespace asmgb
