@@ -48,6 +48,15 @@ enum {
 
 enum { ASM_FP64 = 0, ASM_MIXED = 1 };   /* precision of asm_sample */
 
+/* asm_desc flags */
+/* Test of the failure path (no counterpart in the paper): the record producer
+ * of the sweep kernel withholds every move record and the consumers' bounded
+ * waits give up after a few thousand polls instead of ~4M, so that a run ends
+ * quickly with its timeouts counted and the result calls return
+ * ASM_ERR_TIMEOUT; nothing is in flight when the kernel returns and the
+ * context stays usable.  Never set in production. */
+#define ASM_FLAG_TEST_STALL 0x80000000u
+
 /* asm_sample flags */
 #define ASM_SAMPLE_CONTINUE 1u   /* keep the chains of the previous call and go on */
 #define ASM_SAMPLE_TIMING 2u     /* record CUDA events around every sweep-kernel launch */
@@ -77,7 +86,7 @@ typedef struct asm_problem asm_problem;  /* opaque, library-owned */
  *                of mode j) and U (min(M,n_b) x M, mode-major).  K, G, C are then
  *                unused unless C is also given, which the G-gradient of
  *                asm_backward needs.  This reproduces another implementation's modes.
- *  flags         reserved, 0.
+ *  flags         0, or ASM_FLAG_TEST_STALL (tests of the failure path only).
  *  P, dK_dtheta, dw_dtheta  optional derivatives of the kernel and of the
  *                weights with respect to P grid-density (default-model)
  *                parameters; asm_backward then also returns the theta-gradient. */

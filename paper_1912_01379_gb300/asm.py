@@ -21,6 +21,8 @@ ASM_SAMPLE_CONTINUE = 1
 ASM_SAMPLE_TIMING = 2
 ASM_SAMPLE_MOMENTS = 4
 ASM_SAMPLE_REFRESH_FP64 = 8
+ASM_FLAG_TEST_STALL = 0x80000000   # asm_desc flag: failure-path tests only
+ASM_ERR_TIMEOUT = -10
 ASM_SNAPSHOT_EVERY = 8
 BIN_SWEEPS = 64      # binning: level-0 bin length in sweeps
 BIN_LEVELS = 8       # binning: doubling levels
@@ -161,7 +163,8 @@ def _require_cuda():
     return torch
 
 
-def _make_desc(K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None, prior_shape=None):
+def _make_desc(K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None, prior_shape=None,
+               flags=0):
     """asm_desc of one problem plus the arrays it points into (kept alive by
     the caller until asm_setup returns)."""
     keep = []
@@ -179,6 +182,7 @@ def _make_desc(K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=
     d.n_levels = len(levels)
     d.level_nblocks = nb.ctypes.data_as(_ip)
     d.block_start = bs.ctypes.data_as(_ip)
+    d.flags = int(flags)
     keep += [K, G, C, w, nb, bs]
     if factors is not None:
         arrs = [np.ascontiguousarray(getattr(factors, k), dtype=np.float64) for k in ("Kt", "gt", "d", "V", "U")]
@@ -315,10 +319,11 @@ class Problem(_Handle):
     weights (A = fbar / w).  `factors` (optional) is an object with Kt, gt, d,
     V, U arrays in the layout of asm_desc to use given singular vectors."""
 
-    def __init__(self, K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None, prior_shape=None):
+    def __init__(self, K, G, C, levels, w=None, factors=None, dK_dtheta=None, dw_dtheta=None, prior_shape=None,
+                 flags=0):
         L = load()
         d, self._keep, (self.M, self.N, self.w, self.levels, self.P) = _make_desc(
-            K, G, C, levels, w, factors, dK_dtheta, dw_dtheta, prior_shape)
+            K, G, C, levels, w, factors, dK_dtheta, dw_dtheta, prior_shape, flags)
         h = ct.c_void_p()
         _check(L.asm_setup(ct.byref(d), ct.byref(h)), "asm_setup")
         self._h = h

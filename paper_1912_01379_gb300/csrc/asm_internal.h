@@ -96,6 +96,8 @@ struct LaunchShape {
     int n_items;                      // (problem, chain group) work items
     int minb;                         // register budget: 1 or 2 CTAs per SM
     int prior;                        // 1: kernels with the gamma prior's acceptance step
+    int wait_limit;                   // polls before a bounded mbarrier wait gives up
+    int stall;                        // test of the failure path: the producer issues no records
 };
 
 // Per-launch control block in device memory: the work queue and the launch's
@@ -143,6 +145,10 @@ cudaError_t launch_split_k(const double *KtT, int M, int N, int ldK, float *Khi,
 int sweep_ctas_per_sm_f32(const LaunchShape &shape, int kv, bool batch);
 int sweep_ctas_per_sm_f64(const LaunchShape &shape, int kv, bool batch);
 // Largest supported kv per precision.
+// Polls of a bounded mbarrier wait before it gives up (each poll may suspend
+// the thread briefly); a run that gives up counts a timeout and its results
+// are reported as ASM_ERR_TIMEOUT.
+constexpr int kWaitLimit = 1 << 22;
 // Binning: bins of kBinSweeps kept sweeps aligned to multiples of kBinSweeps in
 // the absolute sweep index (the refresh period), merged pairwise over kBinLevels
 // levels (bins of 64 ... 8192 sweeps).

@@ -417,6 +417,7 @@ struct asm_problem {
     bool refresh_fp64 = false;   // mixed path: FP64 CUDA-core refresh instead of the tensor cores
     int last_team = 0, last_consumers = 0, last_ctas = 0, last_items = 0, last_minb = 0;   // last sweep launch
     bool no_graph = false;    // direct launches only (the allocation-free entry point)
+    bool test_stall = false;  // ASM_FLAG_TEST_STALL: the failure path under test
     // launch bookkeeping
     long long sweep_launches = 0, other_launches = 0, timed_launches = 0;
     double timed_ms = 0.0;
@@ -879,6 +880,8 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
 {
     sh.minb = prior ? 1 : minb;   // the prior's kernels exist for one CTA per SM
     sh.prior = prior ? 1 : 0;
+    sh.wait_limit = kWaitLimit;
+    sh.stall = 0;
     constexpr int kSMs = 152;
     const int TW = 32 / S;
     const int prec = sizeof(T) == 8 ? ASM_FP64 : ASM_MIXED;
@@ -1066,6 +1069,12 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
     LaunchShape sh{};
     if (!plan_shape<T>(sh, S, max_rec, max_np, max_M, total_warps, kv, batch, h->tuned_consumers, minb, prior))
         return ASM_ERR_TOO_LARGE;
+    bool stall = h->test_stall;
+    for (asm_problem *u : us) stall = stall || u->test_stall;
+    if (stall) {   // failure-path test: no records, short waits
+        sh.stall = 1;
+        sh.wait_limit = 4096;
+    }
     // work items, the costliest problems first (a longest-first queue)
     std::vector<int> order(us.size());
     for (size_t k = 0; k < us.size(); ++k) order[k] = (int)k;
@@ -1145,7 +1154,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             key.consumers = sh.consumers;
             key.depth = sh.depth;
             key.n_items = sh.n_items;
-            key.minb = sh.minb + 4 * sh.prior;
+            key.minb = sh.minb + 4 * sh.prior + 8 * sh.stall;
             key.refresh_smem = tc ? refresh_tc_smem(max_bn) + 1 : rsmem;
             key.seed = p0.seed;   // by value in a single problem's launch
             key.problem_id = p0.problem_id;
@@ -1351,6 +1360,8 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
         for (int i = 0; i < N; ++i) p->w[i] = ds->w[i];
     }
 
+    if (ds->flags & ~ASM_FLAG_TEST_STALL) { delete p; return ASM_ERR_ARG; }
+    p->test_stall = (ds->flags & ASM_FLAG_TEST_STALL) != 0;
     if (ds->P < 0 || (ds->P > 0 && (!ds->dK_dtheta || !ds->dw_dtheta))) { delete p; return ASM_ERR_ARG; }
     p->P = ds->P;
     if (p->P > 0 && (!all_finite(ds->dK_dtheta, (size_t)p->P * M * N) || !all_finite(ds->dw_dtheta, (size_t)p->P * N))) {

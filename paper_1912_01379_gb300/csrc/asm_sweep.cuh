@@ -391,7 +391,6 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-constexpr int kWaitLimit = 1 << 22;
 
 // Team-wide bounds from the lanes' keys: signed and unsigned integer minima
 // (FP32: one redux instruction each; FP64: a butterfly of shuffles).
@@ -558,7 +557,7 @@ __device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchSha
                                         unsigned long long *full, unsigned long long *empty,
                                         unsigned char *stages, RingPos &rp, bool &failed)
 {
-    if ((threadIdx.x & 31) != 0 || rg.nsweeps <= 0 || failed) return;
+    if ((threadIdx.x & 31) != 0 || rg.nsweeps <= 0 || failed || sh.stall) return;
     const int D = sh.depth;
     MoveCursor c;
     c.s = rg.sweep0;
@@ -568,7 +567,7 @@ __device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchSha
     const unsigned g0 = rp.g;
     while (!c.done) {
         // the slot's previous record (phase ^ 1) must have been released
-        if (rp.g >= (unsigned)D && !mbar_wait(empty + rp.slot, rp.phase ^ 1u, kWaitLimit)) {
+        if (rp.g >= (unsigned)D && !mbar_wait(empty + rp.slot, rp.phase ^ 1u, sh.wait_limit)) {
             failed = true;
             break;
         }
@@ -584,7 +583,7 @@ __device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchSha
         const unsigned g = rp.g;
         const unsigned from = g > g0 + (unsigned)D ? g - D : g0;
         for (unsigned k = from; k < g; ++k)
-            mbar_wait(full + (k % (unsigned)D), (k / (unsigned)D) & 1u, kWaitLimit);
+            mbar_wait(full + (k % (unsigned)D), (k / (unsigned)D) & 1u, sh.wait_limit);
         atomicAdd(&p.counters->timeouts, 1ull);
     }
 }
@@ -708,7 +707,7 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                 // this move's record: usually landed long ago (one test, one vote)
                 bool ok = mbar_test_wait(full + rp.slot, rp.phase);
                 if (__any_sync(0xffffffffu, !ok)) {
-                    ok = ok || mbar_wait(full + rp.slot, rp.phase, kWaitLimit);
+                    ok = ok || mbar_wait(full + rp.slot, rp.phase, sh.wait_limit);
                     if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
                         failed = true;
                         break;
