@@ -22,6 +22,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <type_traits>
 #include <math_constants.h>
 
 #include "asm_internal.h"
@@ -426,19 +427,22 @@ __device__ __forceinline__ void lds_v(const double *p, double (&o)[2])
 
 // f += delta * V (clamped at +0) and the lane's bound keys of the next mode,
 // rows read from a shared-memory stage.
-// The caller loads chunk 0 (v0, r0) ahead of the draw; kcnt >= 1.
-template <class T, int KV>
+// The caller loads chunk 0 (v0, r0) ahead of the draw; kcnt >= 1.  The pass
+// covers chunks 0 .. KK-1; with CHK each is tested against kcnt, without it
+// all KK are present (kcnt == KK), so the loop has no branch.
+template <class T, int KV, int KK = KV, bool CHK = true>
 __device__ __forceinline__ void fused_pass_smem(T (&f)[KV][VecOf<T>::n], T delta, const T (&v0)[VecOf<T>::n],
                                                 const T (&r0)[VecOf<T>::n], const T *vrow, const T *rrow,
                                                 int kcnt, int sl, int S, typename BoundKey<T>::S &lk,
                                                 typename BoundKey<T>::U &hk)
 {
     constexpr int VEC = VecOf<T>::n;
+    static_assert(KK >= 1 && KK <= KV, "chunk count");
     lk = BoundKey<T>::lo0;
     hk = BoundKey<T>::hi0;
 #pragma unroll
-    for (int k = 0; k < KV; ++k) {
-        if (k < kcnt) {
+    for (int k = 0; k < KK; ++k) {
+        if (!CHK || k < kcnt) {
             const int idx = VEC * (k * S + sl);
             T vv[VEC], rr[VEC];
             if (k == 0) {
@@ -671,115 +675,136 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
             typename BoundKey<T>::S lk;
             typename BoundKey<T>::U hk;
             fused_pass<T, KV>(f, T(0), p.pd.V + B.offV, p.pd.R + B.offR, kcnt, sl, S, lk, hk);  // keys of mode 0
-            for (int j = 0; j < B.n; ++j) {
-                // what does not depend on the bounds first: c_j and the uniform
-                const T cj = j < B.np ? csm[j] : T(0);
-                // uniform of move t: word t%4 of Philox(ctr = {t/4, s, q, problem}); the 4S
-                // uniforms of a window come from one Philox call per lane (lane sl: ctr
-                // win/4 + sl, moves win + 4 sl + 0..3)
-                const int t = B.start + j;
-                if (t >= win_end) {
-                    win = (t / (4 * S)) * (4 * S);
-                    win_end = win + 4 * S;
-                    unsigned long long c0 = (unsigned long long)(win >> 2) + (unsigned long long)sl;
-                    unsigned long long c1 = (unsigned long long)s, c2 = (unsigned long long)q + p.chain_offset,
-                                       c3 = p.problem_id;
-                    philox4x64_10(c0, c1, c2, c3, p.seed, 0ull);
-                    __syncwarp();   // the previous window is read by every lane
-                    usm[4 * sl] = uniform_from<T>(c0);
-                    usm[4 * sl + 1] = uniform_from<T>(c1);
-                    usm[4 * sl + 2] = uniform_from<T>(c2);
-                    usm[4 * sl + 3] = uniform_from<T>(c3);
-                    if constexpr (PRIOR) {   // acceptance uniforms: ctr {t/4, s, q, problem xor 2^63}
-                        c0 = (unsigned long long)(win >> 2) + (unsigned long long)sl;
-                        c1 = (unsigned long long)s;
-                        c2 = (unsigned long long)q + p.chain_offset;
-                        c3 = p.problem_id ^ (1ull << 63);
+            // The block's moves.  Where the lane's chunk count is 1 (blocks of at most
+            // VEC*S points) or KV (every chunk present) it is a compile-time constant and
+            // the move loop tests no chunk; the uniforms are refilled once per window of
+            // 4S moves, outside the loop over the window's moves.
+            auto block_moves = [&](auto chunks) {
+                constexpr int KC = decltype(chunks)::value;   // 0: kcnt chunks, each tested
+                constexpr int KK = KC ? KC : KV;
+                constexpr bool CHK = KC == 0;
+                for (int j = 0; j < B.n && !failed;) {
+                    // uniform of move t: word t%4 of Philox(ctr = {t/4, s, q, problem}); the 4S
+                    // uniforms of a window come from one Philox call per lane (lane sl: ctr
+                    // win/4 + sl, moves win + 4 sl + 0..3)
+                    const int t0 = B.start + j;
+                    if (t0 >= win_end) {
+                        win = (t0 / (4 * S)) * (4 * S);
+                        win_end = win + 4 * S;
+                        unsigned long long c0 = (unsigned long long)(win >> 2) + (unsigned long long)sl;
+                        unsigned long long c1 = (unsigned long long)s, c2 = (unsigned long long)q + p.chain_offset,
+                                           c3 = p.problem_id;
                         philox4x64_10(c0, c1, c2, c3, p.seed, 0ull);
-                        usm[4 * S + 4 * sl] = uniform_from<T>(c0);
-                        usm[4 * S + 4 * sl + 1] = uniform_from<T>(c1);
-                        usm[4 * S + 4 * sl + 2] = uniform_from<T>(c2);
-                        usm[4 * S + 4 * sl + 3] = uniform_from<T>(c3);
+                        __syncwarp();   // the previous window is read by every lane
+                        usm[4 * sl] = uniform_from<T>(c0);
+                        usm[4 * sl + 1] = uniform_from<T>(c1);
+                        usm[4 * sl + 2] = uniform_from<T>(c2);
+                        usm[4 * sl + 3] = uniform_from<T>(c3);
+                        if constexpr (PRIOR) {   // acceptance uniforms: ctr {t/4, s, q, problem xor 2^63}
+                            c0 = (unsigned long long)(win >> 2) + (unsigned long long)sl;
+                            c1 = (unsigned long long)s;
+                            c2 = (unsigned long long)q + p.chain_offset;
+                            c3 = p.problem_id ^ (1ull << 63);
+                            philox4x64_10(c0, c1, c2, c3, p.seed, 0ull);
+                            usm[4 * S + 4 * sl] = uniform_from<T>(c0);
+                            usm[4 * S + 4 * sl + 1] = uniform_from<T>(c1);
+                            usm[4 * S + 4 * sl + 2] = uniform_from<T>(c2);
+                            usm[4 * S + 4 * sl + 3] = uniform_from<T>(c3);
+                        }
+                        __syncwarp();
                     }
-                    __syncwarp();
-                }
-                const T u = usm[t - win];
-                // this move's record: usually landed long ago (one test, one vote)
-                bool ok = mbar_test_wait(full + rp.slot, rp.phase);
-                if (__any_sync(0xffffffffu, !ok)) {
-                    ok = ok || mbar_wait(full + rp.slot, rp.phase, sh.wait_limit);
-                    if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
-                        failed = true;
-                        break;
-                    }
-                }
-                const T *st = reinterpret_cast<const T *>(stages + (size_t)rp.slot * sh.stage_bytes);
-                const T dj = st[2 * B.rs], ij = st[2 * B.rs + 1];
-                T v0[VEC], r0[VEC];   // chunk 0 of the pass: independent of the draw, loaded first
-                lds_v(st + VEC * sl, v0);
-                lds_v(st + B.rs + VEC * sl, r0);
-
-                T lo, hi;
-                team_bounds(lk, hk, lo, hi, S, team_base);
-                // degenerate interval: no move; zero mode: flat on [lo, hi]; else the
-                // truncated Gaussian (the only branch)
-                const bool open = hi > lo;
-                T delta = m_fma(u, hi - lo, lo);
-                if (open && dj != T(0)) delta = tn_step<T>(cj, dj, ij, lo, hi, u, capped);
-                n_deg += open ? 0u : 1u;
-                n_zero += (open && dj == T(0)) ? 1u : 0u;
-                delta = open ? delta : T(0);
-                const bool fin = isfinite(delta);
-                n_bad += fin ? 0u : 1u;
-                delta = fin ? delta : T(0);
-                if constexpr (PRIOR) if (delta != T(0)) {
-                    // gamma prior (Eq. compat): the draw is a proposal, accepted with
-                    // probability min(1, prod ((f + delta V)_+ / f)^(a - 1)) over the block
-                    T lsum = T(0);
-                    unsigned zflags = 0u;   // 1: a proposed value is 0, 2: a current value is 0
-#pragma unroll
-                    for (int k = 0; k < KV; ++k) {
-                        if (k < kcnt) {
-                            T vv[VEC];
-                            if (k == 0) {
-#pragma unroll
-                                for (int v = 0; v < VEC; ++v) vv[v] = v0[v];
-                            } else {
-                                lds_v(st + VEC * (k * S + sl), vv);
+                    const int jend = min(B.n, win_end - B.start);   // this window's moves in the block
+                    for (; j < jend; ++j) {
+                        // what does not depend on the bounds first: c_j and the uniform
+                        const T cj = j < B.np ? csm[j] : T(0);
+                        const int t = B.start + j;
+                        const T u = usm[t - win];
+                        // this move's record: usually landed long ago (one test, one vote)
+                        bool ok = mbar_test_wait(full + rp.slot, rp.phase);
+                        if (__any_sync(0xffffffffu, !ok)) {
+                            ok = ok || mbar_wait(full + rp.slot, rp.phase, sh.wait_limit);
+                            if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
+                                failed = true;
+                                break;
                             }
+                        }
+                        const T *st = reinterpret_cast<const T *>(stages + (size_t)rp.slot * sh.stage_bytes);
+                        const T dj = st[2 * B.rs], ij = st[2 * B.rs + 1];
+                        T v0[VEC], r0[VEC];   // chunk 0 of the pass: independent of the draw, loaded first
+                        lds_v(st + VEC * sl, v0);
+                        lds_v(st + B.rs + VEC * sl, r0);
+
+                        T lo, hi;
+                        team_bounds(lk, hk, lo, hi, S, team_base);
+                        // degenerate interval: no move; zero mode: flat on [lo, hi]; else the
+                        // truncated Gaussian (the only branch)
+                        const bool open = hi > lo;
+                        T delta = m_fma(u, hi - lo, lo);
+                        if (open && dj != T(0)) delta = tn_step<T>(cj, dj, ij, lo, hi, u, capped);
+                        n_deg += open ? 0u : 1u;
+                        n_zero += (open && dj == T(0)) ? 1u : 0u;
+                        delta = open ? delta : T(0);
+                        const bool fin = isfinite(delta);
+                        n_bad += fin ? 0u : 1u;
+                        delta = fin ? delta : T(0);
+                        if constexpr (PRIOR) if (delta != T(0)) {
+                            // gamma prior (Eq. compat): the draw is a proposal, accepted with
+                            // probability min(1, prod ((f + delta V)_+ / f)^(a - 1)) over the block
+                            T lsum = T(0);
+                            unsigned zflags = 0u;   // 1: a proposed value is 0, 2: a current value is 0
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) {
-                                const int nl = VEC * (k * S + sl) + v;
-                                if (nl < B.n) {
-                                    const T am1 = __ldg(p.prior_am1 + B.start + nl);
-                                    if (am1 != T(0)) {
-                                        const T x0 = f[k][v];
-                                        const T x1 = m_max(m_fma(delta, vv[v], x0), T(0));
-                                        if (x1 == T(0)) zflags |= 1u;
-                                        else if (x0 == T(0)) zflags |= 2u;
-                                        else lsum += am1 * (m_log(x1) - m_log(x0));
+                            for (int k = 0; k < KV; ++k) {
+                                if (k < kcnt) {
+                                    T vv[VEC];
+                                    if (k == 0) {
+#pragma unroll
+                                        for (int v = 0; v < VEC; ++v) vv[v] = v0[v];
+                                    } else {
+                                        lds_v(st + VEC * (k * S + sl), vv);
+                                    }
+#pragma unroll
+                                    for (int v = 0; v < VEC; ++v) {
+                                        const int nl = VEC * (k * S + sl) + v;
+                                        if (nl < B.n) {
+                                            const T am1 = __ldg(p.prior_am1 + B.start + nl);
+                                            if (am1 != T(0)) {
+                                                const T x0 = f[k][v];
+                                                const T x1 = m_max(m_fma(delta, vv[v], x0), T(0));
+                                                if (x1 == T(0)) zflags |= 1u;
+                                                else if (x0 == T(0)) zflags |= 2u;
+                                                else lsum += am1 * (m_log(x1) - m_log(x0));
+                                            }
+                                        }
                                     }
                                 }
                             }
+                            for (int off = 1; off < S; off <<= 1) {
+                                lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+                                zflags |= __shfl_xor_sync(0xffffffffu, zflags, off);
+                            }
+                            const T lr = (zflags & 1u) ? -CUDART_INF_F : (zflags & 2u) ? CUDART_INF_F : lsum;
+                            const T ua = usm[4 * S + (t - win)];
+                            if (!(m_log(ua) < lr)) {
+                                delta = T(0);
+                                ++n_rej;
+                            }
                         }
-                    }
-                    for (int off = 1; off < S; off <<= 1) {
-                        lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
-                        zflags |= __shfl_xor_sync(0xffffffffu, zflags, off);
-                    }
-                    const T lr = (zflags & 1u) ? -CUDART_INF_F : (zflags & 2u) ? CUDART_INF_F : lsum;
-                    const T ua = usm[4 * S + (t - win)];
-                    if (!(m_log(ua) < lr)) {
-                        delta = T(0);
-                        ++n_rej;
+                        fused_pass_smem<T, KV, KK, CHK>(f, delta, v0, r0, st, st + B.rs, kcnt, sl, S, lk, hk);
+                        if (j < B.np && sl == 0) wsm[j] = dj * delta;
+                        // release the record to the producer (one arrival per warp)
+                        __syncwarp();
+                        mbar_arrive_lane0(empty + rp.slot, lane);
+                        ring_next(rp, D);
                     }
                 }
-                fused_pass_smem<T, KV>(f, delta, v0, r0, st, st + B.rs, kcnt, sl, S, lk, hk);
-                if (j < B.np && sl == 0) wsm[j] = dj * delta;
-                // release the record to the producer (one arrival per warp)
-                __syncwarp();
-                mbar_arrive_lane0(empty + rp.slot, lane);
-                ring_next(rp, D);
+            };
+            if (kcnt == 1) {
+                block_moves(std::integral_constant<int, 1>{});
+            } else if constexpr (KV > 1) {
+                if (kcnt == KV)
+                    block_moves(std::integral_constant<int, KV>{});
+                else
+                    block_moves(std::integral_constant<int, 0>{});
             }
             if (failed) break;
             __syncwarp();
