@@ -7,7 +7,7 @@
  * recomputes the mode coordinate by a dot product, exactly as Sec. IV.D counts
  * the work.  No blocking, fusion or incremental bookkeeping.
  *
- * Readings of the paper that this file fixes (all also listed in the design doc):
+ * Readings of the paper that this file fixes:
  *  R1 moves draw delta = e' - e from the 1-D conditional with ONE uniform u
  *     through the inverse CDF of the truncated normal (Sec. IV.A cites a
  *     rejection sampler; an inverse CDF samples the same distribution).  The
