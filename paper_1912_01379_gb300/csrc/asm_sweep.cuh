@@ -595,8 +595,11 @@ __device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchSha
 // --------------------------------------------------------------------------
 // A consumer warp: its team(s) of S lanes run the chains of chain group
 // `group` (consumers x 32/S chains) of problem p for the launch's sweeps.
+// WIDE: the block entry/exit projections keep sixteen loads in flight instead
+// of eight (same accumulation order); it pays in the kernels budgeted for two
+// CTAs per SM and costs a little in the 255-register ones.
 // --------------------------------------------------------------------------
-template <class T, int KV, bool PRIOR>
+template <class T, int KV, bool PRIOR, bool WIDE>
 __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchShape &sh, const SweepRange &rg,
                                         int group, unsigned char *smem_raw, unsigned long long *full,
                                         unsigned long long *empty, unsigned char *stages, RingPos &rp,
@@ -653,13 +656,23 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     const int nl = VEC * (k * S + sl) + v;
                     f[k][v] = (k < kcnt && nl < B.n) ? Fq[B.start + nl] : T(0);
                 }
-            // c = U_b^T r~ (lanes split the modes; eight loads in flight, eight partial sums)
+            // c = U_b^T r~ (lanes split the modes; eight (WIDE: sixteen) loads in flight, eight
+            // partial sums, partial sum i taking the terms m = i mod 8 in increasing m)
             const T *Um = p.pd.Um + B.offU;
             for (int j = sl; j < B.np; j += S) {
                 T a[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) a[i] = T(0);
                 int m = 0;
+                if constexpr (WIDE) {
+                    for (; m + 15 < p.M; m += 16) {
+                        T x[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) x[i] = __ldg(Um + (size_t)(m + i) * B.np + j);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) a[i & 7] = m_fma(x[i], rsm[m + i], a[i & 7]);
+                    }
+                }
                 for (; m + 7 < p.M; m += 8) {
                     T x[8];
 #pragma unroll
@@ -808,13 +821,23 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
             }
             if (failed) break;
             __syncwarp();
-            // exit: r~ -= U_b w (lanes split the data points; eight loads in flight, eight partial sums)
+            // exit: r~ -= U_b w (lanes split the data points; eight (WIDE: sixteen) loads in
+            // flight, eight partial sums as at entry)
             const T *Ut = p.pd.Ut + B.offU;
             for (int m = sl; m < p.M; m += S) {
                 T a[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) a[i] = T(0);
                 int j = 0;
+                if constexpr (WIDE) {
+                    for (; j + 15 < B.np; j += 16) {
+                        T x[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) x[i] = __ldg(Ut + (size_t)(j + i) * p.M + m);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) a[i & 7] = m_fma(x[i], wsm[j + i], a[i & 7]);
+                    }
+                }
                 for (; j + 7 < B.np; j += 8) {
                     T x[8];
 #pragma unroll
@@ -909,7 +932,7 @@ __global__ void __launch_bounds__(32 * (kMaxConsumers + 1), MINB) sweep_kernel(c
         if (wcta == shape.consumers)
             produce(p, shape, rg, full, empty, stages, rp, failed);
         else
-            consume<T, KV, PRIOR>(p, shape, rg, w.group, smem_raw, full, empty, stages, rp, failed);
+            consume<T, KV, PRIOR, (MINB > 1)>(p, shape, rg, w.group, smem_raw, full, empty, stages, rp, failed);
         __syncthreads();   // the item is finished before sp and s_item change
     }
 }
