@@ -144,7 +144,10 @@ typedef struct {
  * |component| of each V_j positive; d <= d_1 max(M,n_b) 2^-52 counts as a zero
  * mode, and so does d <= d_1 max(M,n_b) 2^-40 when V_j changes sign (below
  * that level U_j = K~ V_j / d_j is not resolvable in FP64 while the likelihood
- * is flat along V_j over its positivity interval).  On success *out receives a new handle (free with asm_destroy). */
+ * is flat along V_j over its positivity interval).  On success *out receives a new handle (free with asm_destroy);
+ * on failure *out is NULL and nothing stays allocated.  The environment variable
+ * ASM_TEAM_LANES = 8, 16 or 32, read here, fixes the lanes per chain of the
+ * handle's sweep launches (testing; other values are ignored, asm_tune overrides it). */
 int asm_setup(const asm_desc *d, asm_problem **out);
 
 /* Set-up of n independent problems as one batch handle (each problem as in

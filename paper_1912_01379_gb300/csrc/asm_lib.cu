@@ -1317,6 +1317,7 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
     if (M < 1 || N < 1 || ds->n_levels < 1 || !ds->level_nblocks || !ds->block_start) return ASM_ERR_SHAPE;
     const bool given = ds->Kt && ds->gt && ds->d && ds->V && ds->U;
     if (!given && (!ds->K || !ds->G || !ds->C)) return ASM_ERR_ARG;
+    // from here on every failure path releases what the handle holds with asm_destroy
     asm_problem *p = new (std::nothrow) asm_problem;
     if (!p) return ASM_ERR_ARG;
     p->M = M;
@@ -1324,7 +1325,7 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
     p->n_levels = ds->n_levels;
     int nb = 0;
     for (int l = 0; l < ds->n_levels; ++l) {
-        if (ds->level_nblocks[l] < 1) { delete p; return ASM_ERR_SHAPE; }
+        if (ds->level_nblocks[l] < 1) { asm_destroy(p); return ASM_ERR_SHAPE; }
         p->level_first.push_back(nb);
         p->level_nblocks.push_back(ds->level_nblocks[l]);
         nb += ds->level_nblocks[l];
@@ -1335,7 +1336,7 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
         const int *st = ds->block_start + p->level_first[l];
         for (int b = 0; b < ds->level_nblocks[l]; ++b) {
             const int s0 = st[b], s1 = b + 1 < ds->level_nblocks[l] ? st[b + 1] : N;
-            if ((b == 0 && s0 != 0) || s1 <= s0 || s1 > N) { delete p; return ASM_ERR_SHAPE; }
+            if ((b == 0 && s0 != 0) || s1 <= s0 || s1 > N) { asm_destroy(p); return ASM_ERR_SHAPE; }
             BlockDesc B{};
             B.start = s0;
             B.n = s1 - s0;
@@ -1356,16 +1357,16 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
     p->totV = oV; p->totR = oR; p->totd = od; p->totU = oU; p->totRec = oRec;
     p->w.assign(N, 1.0);
     if (ds->w) {
-        if (!all_finite(ds->w, N)) { delete p; return ASM_ERR_NONFINITE; }
+        if (!all_finite(ds->w, N)) { asm_destroy(p); return ASM_ERR_NONFINITE; }
         for (int i = 0; i < N; ++i) p->w[i] = ds->w[i];
     }
 
-    if (ds->flags & ~ASM_FLAG_TEST_STALL) { delete p; return ASM_ERR_ARG; }
+    if (ds->flags & ~ASM_FLAG_TEST_STALL) { asm_destroy(p); return ASM_ERR_ARG; }
     p->test_stall = (ds->flags & ASM_FLAG_TEST_STALL) != 0;
-    if (ds->P < 0 || (ds->P > 0 && (!ds->dK_dtheta || !ds->dw_dtheta))) { delete p; return ASM_ERR_ARG; }
+    if (ds->P < 0 || (ds->P > 0 && (!ds->dK_dtheta || !ds->dw_dtheta))) { asm_destroy(p); return ASM_ERR_ARG; }
     p->P = ds->P;
     if (p->P > 0 && (!all_finite(ds->dK_dtheta, (size_t)p->P * M * N) || !all_finite(ds->dw_dtheta, (size_t)p->P * N))) {
-        delete p;
+        asm_destroy(p);
         return ASM_ERR_NONFINITE;
     }
     // gamma prior (Eq. compat): shapes a_n >= 1; all 1 is the flat measure
@@ -1374,8 +1375,8 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
         bool any = false;
         for (int n = 0; n < N; ++n) {
             const double a = ds->prior_shape[n];
-            if (!std::isfinite(a)) { delete p; return ASM_ERR_NONFINITE; }
-            if (!(a >= 1.0)) { delete p; return ASM_ERR_ARG; }
+            if (!std::isfinite(a)) { asm_destroy(p); return ASM_ERR_NONFINITE; }
+            if (!(a >= 1.0)) { asm_destroy(p); return ASM_ERR_ARG; }
             any = any || a != 1.0;
         }
         if (any) {
@@ -1386,7 +1387,7 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
     HostFactors hf;
     int rc = ASM_OK;
     if (given) {
-        if (!all_finite(ds->Kt, (size_t)M * N) || !all_finite(ds->gt, M)) { delete p; return ASM_ERR_NONFINITE; }
+        if (!all_finite(ds->Kt, (size_t)M * N) || !all_finite(ds->gt, M)) { asm_destroy(p); return ASM_ERR_NONFINITE; }
         hf.Kt.assign(ds->Kt, ds->Kt + (size_t)M * N);
         hf.gt.assign(ds->gt, ds->gt + M);
         const double *dd = ds->d, *dv = ds->V, *du = ds->U;
@@ -1399,14 +1400,14 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
         }
     } else {
         if (!all_finite(ds->K, (size_t)M * N) || !all_finite(ds->G, M) || !all_finite(ds->C, (size_t)M * M)) {
-            delete p;
+            asm_destroy(p);
             return ASM_ERR_NONFINITE;
         }
         rc = device_factorize(ds, p, hf, &p->d_L);
-        if (rc != ASM_OK) { delete p; return rc; }
+        if (rc != ASM_OK) { asm_destroy(p); return rc; }
     }
     if (given && ds->C) {
-        if (!all_finite(ds->C, (size_t)M * M)) { delete p; return ASM_ERR_NONFINITE; }
+        if (!all_finite(ds->C, (size_t)M * M)) { asm_destroy(p); return ASM_ERR_NONFINITE; }
         rc = device_cholesky(ds->C, M, &p->d_L);
         if (rc != ASM_OK) { asm_destroy(p); return rc; }
     }
@@ -1440,7 +1441,7 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
                 pos |= v[i] > 0.0;
                 neg |= v[i] < 0.0;
             }
-            if (!(pos && neg)) { delete p; return ASM_ERR_IMPROPER; }
+            if (!(pos && neg)) { asm_destroy(p); return ASM_ERR_IMPROPER; }
         }
     }
     // starting scale: s* = argmin_{s >= 0} |g~ - s K~ 1|^2 (flat default model)
@@ -1487,7 +1488,7 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
     const char *team = std::getenv("ASM_TEAM_LANES");
     if (team) {
         const int t = std::atoi(team);
-        if (t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32) p->team = t;
+        if (t == 8 || t == 16 || t == 32) p->team = t;
     }
     *out = p;
     return ASM_OK;
