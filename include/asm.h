@@ -215,7 +215,8 @@ size_t asm_workspace_bytes(const asm_problem *p, int chains, int precision);
  * same workspace (same chains, seed and precision) without resetting the sums;
  * otherwise chains start from the flat default-model scale fit.
  * ASM_SAMPLE_TIMING records a CUDA event pair on `stream` around every sweep
- * launch; asm_status reports their summed duration.
+ * launch; asm_status reports their summed duration.  Any other flag bit:
+ * ASM_ERR_ARG.
  * Launches: one persistent sweep kernel per refresh period (64 sweeps) over
  * every (problem, chain group) work item, then the FP64 residual refresh.
  * Runs of whole periods replay a CUDA graph of (advance the sweep range,

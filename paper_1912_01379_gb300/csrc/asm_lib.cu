@@ -1635,6 +1635,8 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
 {
     if (!p || chains < 1 || burn_in < 0 || sweeps < 0) return ASM_ERR_ARG;
     if (precision != ASM_FP64 && precision != ASM_MIXED) return ASM_ERR_ARG;
+    if (flags & ~(ASM_SAMPLE_CONTINUE | ASM_SAMPLE_TIMING | ASM_SAMPLE_MOMENTS | ASM_SAMPLE_REFRESH_FP64))
+        return ASM_ERR_ARG;
     const bool moments = (flags & ASM_SAMPLE_MOMENTS) != 0;
     if (moments && !p->kids.empty()) return ASM_ERR_ARG;   // backward moments: single problems
     const RunLayout RL = run_layout(p, chains, precision);
