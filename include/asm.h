@@ -313,9 +313,12 @@ int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, ui
 int asm_set_stream_ids(asm_problem *p, uint64_t problem_id, uint64_t chain_offset);
 
 /* Checkpoint of the run state (synchronises): chain states, tracked residuals,
- * sums, counters and the sweep count, so that a restored run continues bit for
- * bit.  host_buf NULL: *bytes receives the size needed.  Otherwise *bytes is
- * the buffer size on input and the bytes written on output. */
+ * sums, bins of the Monte Carlo error, counters, the sweep count and the start
+ * of the kept run, so that a restored run continues bit for bit (averages and
+ * binned errors alike).  host_buf NULL: *bytes receives the size needed.
+ * Otherwise *bytes is the buffer size on input and the bytes written on
+ * output.  The blob is versioned; asm_restore accepts only the version this
+ * library writes (ASM_ERR_ARG otherwise). */
 int asm_checkpoint(asm_problem *p, void *host_buf, size_t *bytes);
 
 /* Restore a checkpoint into d_workspace (>= asm_workspace_bytes for the

@@ -2026,7 +2026,9 @@ struct CheckpointHeader {
     int64_t M, N, chains, precision;
     uint64_t seed, problem_id, chain_offset;
     int64_t sweeps_done, kept, ws_bytes;
+    int64_t kept_since;   // first sweep of the unbroken kept run (binning of a continuation)
 };
+constexpr uint64_t kCheckpointVersion = 2;
 constexpr uint64_t kCheckpointMagic = 0x41534d434b505431ull;   // "ASMCKPT1"
 }  // namespace
 
@@ -2041,8 +2043,8 @@ int asm_checkpoint(asm_problem *p, void *host_buf, size_t *bytes)
         return ASM_OK;
     }
     if (*bytes < need) return ASM_ERR_ARG;
-    CheckpointHeader h{kCheckpointMagic, 1, p->M, p->N, p->chains, p->precision, p->seed, p->problem_id,
-                       p->chain_offset, p->sweeps_done, p->kept, (int64_t)L.total};
+    CheckpointHeader h{kCheckpointMagic, kCheckpointVersion, p->M, p->N, p->chains, p->precision, p->seed,
+                       p->problem_id, p->chain_offset, p->sweeps_done, p->kept, (int64_t)L.total, p->kept_since};
     std::memcpy(host_buf, &h, sizeof(h));
     if (cudaMemcpyAsync((char *)host_buf + sizeof(h), p->ws, L.total, cudaMemcpyDeviceToHost, p->stream) !=
             cudaSuccess ||
@@ -2058,7 +2060,7 @@ int asm_restore(asm_problem *p, const void *host_buf, size_t bytes, void *d_work
     if (!p || !host_buf || bytes < sizeof(CheckpointHeader) || !p->kids.empty()) return ASM_ERR_ARG;
     CheckpointHeader h;
     std::memcpy(&h, host_buf, sizeof(h));
-    if (h.magic != kCheckpointMagic || h.version != 1) return ASM_ERR_ARG;
+    if (h.magic != kCheckpointMagic || h.version != kCheckpointVersion) return ASM_ERR_ARG;
     if (h.M != p->M || h.N != p->N) return ASM_ERR_SHAPE;
     if (h.precision != ASM_FP64 && h.precision != ASM_MIXED) return ASM_ERR_ARG;
     const WsLayout L = ws_layout(p, (int)h.chains, (int)h.precision);
@@ -2078,6 +2080,7 @@ int asm_restore(asm_problem *p, const void *host_buf, size_t bytes, void *d_work
     p->chain_offset = p->next_chain_offset = h.chain_offset;
     p->sweeps_done = h.sweeps_done;
     p->kept = h.kept;
+    p->kept_since = h.kept_since;
     p->sweep_launches = p->other_launches = p->timed_launches = 0;
     p->timed_ms = 0.0;
     p->timing = false;

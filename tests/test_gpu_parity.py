@@ -231,3 +231,9 @@ def test_checkpoint_restore_continues_bit_for_bit(precision):
     assert np.array_equal(f_b, f_ref)
     assert np.array_equal(chi_b, chi_ref)
     assert np.array_equal(b.average()["mean_fbar"], avg_ref["mean_fbar"])
+    # the bins of the Monte Carlo error continue too: the restored run keeps the start of
+    # the kept sweeps, so the bin that holds burn-in sweeps stays out on both sides
+    me_b, me_ref = b.mc_error(), ref.mc_error()
+    assert np.array_equal(me_b["bins_per_chain"], me_ref["bins_per_chain"])
+    assert np.array_equal(me_b["sigma2_levels"], me_ref["sigma2_levels"], equal_nan=True)
+    assert np.array_equal(me_b["ess"], me_ref["ess"], equal_nan=True)
