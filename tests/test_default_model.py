@@ -3,7 +3,7 @@ the fitted Gaussian width for the paper's optical-conductivity test case
 matches the value the paper reads off its fit (tests/golden/default_model_fit.txt),
 Pi_def has the sum rule at omega_m = 0 and tends to 0 at large omega_m for every
 family, and the paper's Lorentzian grid of width 2.5 misfits the data far more
-than the fitted densities (the paper: it "does not even remotely represent" the data)."""
+than the fitted densities (the paper finds that grid far from representing the data)."""
 import math
 import os
 
