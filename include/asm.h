@@ -64,6 +64,16 @@ enum { ASM_FP64 = 0, ASM_MIXED = 1 };   /* precision of asm_sample */
 #define ASM_SAMPLE_REFRESH_FP64 8u  /* ASM_MIXED: refresh residuals on FP64 CUDA cores, not 3xTF32 tensor cores */
 #define ASM_SNAPSHOT_EVERY 8     /* kept sweeps between snapshots of all chains */
 
+/* Environment variables the library reads (testing and tuning only; no result
+ * depends on them, every chain does the same arithmetic under every launch
+ * shape; values outside the ranges below are ignored):
+ *   ASM_TEAM_LANES         8, 16 or 32: lanes per chain of a handle, read by
+ *                          asm_setup (asm_tune replaces it);
+ *   ASM_CONSUMERS_PER_CTA  1..7: chain warps per CTA of every sweep launch
+ *                          (takes precedence over the heuristic and asm_tune);
+ *   ASM_RING_DEPTH         2..16: stages of the move-record ring (default: as
+ *                          many as shared memory holds, at most 16). */
+
 typedef struct asm_problem asm_problem;  /* opaque, library-owned */
 
 /* Problem description (Sec. II, Eq. likelihood and Eq. matrixeq; Sec. IV.C).
