@@ -209,9 +209,9 @@ def batch_problems(seed: int = 1003, n_problems: int = 256, chains: int = 64):
             s = min(s, rem)
             sizes.append(s)
             rem -= s
-        if len(sizes) > 1 and sizes[-1] < 25:
-            last = sizes.pop()
-            sizes[-1] += last
+        if len(sizes) > 1 and sizes[-1] < 25:   # a short tail joins its neighbour, in two halves if > 100
+            joined = sizes.pop() + sizes.pop()
+            sizes += [joined] if joined <= 100 else [joined // 2, joined - joined // 2]
         levels = [[0], contiguous_blocks(N, sizes)]
         C = np.eye(M) * sig * sig
         out.append(_make(f"batch{p}_{'bos' if bos else 'fer'}_M{M}_N{N}", K, A * w, C, omega, w,
