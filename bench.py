@@ -68,6 +68,8 @@ def _args():
                     help="sweeps per grid of the paper-test-case side measurement (0: skip)")
     ap.add_argument("--hierarchy-sweeps", type=int, default=3000,
                     help="sweeps per partition scheme of the hierarchy side measurement (0: skip)")
+    ap.add_argument("--diff-sweeps", type=int, default=0,
+                    help="kept sweeps per run of the differentiation side measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -293,6 +295,40 @@ def hierarchy_side(args, asm, torch, stream):
     return out
 
 
+def diff_side(args, asm, torch, stream):
+    """Differentiation workload (N_tau = 64, N_omega = 200 on the grid of an
+    8-parameter Gaussian-mixture density on [-6, 6], beta = 16, noise 1e-4,
+    4096 chains, global level plus 8 blocks of 25): mixed-precision sampling
+    with the snapshot moments, then the vector-Jacobian products of <A> with
+    respect to G and the 8 grid parameters (asm_backward).  Four runs with
+    different seeds give the standard error of each product."""
+    p = W.theta_problem()
+    chains, burn, sweeps, runs = p.chains, 500, args.diff_sweeps, 4
+    gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w, dK_dtheta=p.extra["dK_dtheta"],
+                     dw_dtheta=p.extra["dw_dtheta"])
+    v = np.random.default_rng(7).standard_normal(p.N)
+    t_sample, t_back, gG, gT = [], [], [], []
+    for r in range(runs):
+        t_sample.append(_timed(torch, stream, lambda: gp.sample(chains, burn, sweeps, 100 + r,
+                                                                precision=asm.ASM_MIXED, moments=True)))
+        t0 = time.perf_counter()
+        g, t = gp.backward(v)
+        t_back.append(time.perf_counter() - t0)
+        gG.append(g)
+        gT.append(t)
+    gG, gT = np.array(gG), np.array(gT)
+
+    def rel_sem(x):
+        return float(np.linalg.norm(x.std(axis=0, ddof=1) / np.sqrt(runs)) / np.linalg.norm(x.mean(axis=0)))
+
+    return {"workload": "differentiation_b16_Ntau64_Nomega200_theta8_4096chains", "chains": chains,
+            "burn_in": burn, "sweeps": sweeps, "runs": runs,
+            "updates_per_s": chains * (burn + sweeps) * p.N / float(np.mean(t_sample)),
+            "backward_ms": 1e3 * float(np.mean(t_back)),
+            "grad_G_rel_sem": rel_sem(gG), "grad_theta_rel_sem": rel_sem(gT),
+            "grad_theta": gT.mean(axis=0).tolist()}
+
+
 def paper_side(args, asm, torch, stream):
     """The paper's own test case (optical conductivity model 2, accurate data,
     60 bosonic Matsubara frequencies, beta = 15) over the full partition
@@ -474,6 +510,7 @@ def main():
     grid = grid_side(args, asm, torch, stream) if (args.grid_sweeps > 0 and rank == 0) else None
     hier = hierarchy_side(args, asm, torch, stream) if (args.hierarchy_sweeps > 0 and rank == 0) else None
     paper = paper_side(args, asm, torch, stream) if (args.paper_sweeps > 0 and rank == 0) else None
+    diff = diff_side(args, asm, torch, stream) if (args.diff_sweeps > 0 and rank == 0) else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -502,6 +539,7 @@ def main():
             "grid_sweep": grid,
             "partition_schemes": hier,
             "paper_test_case": paper,
+            "differentiation": diff,
             "gpu_launches": int(sweep_launches + other_launches + args.steps),
             "clocks": clocks,
         }
