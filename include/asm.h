@@ -287,14 +287,18 @@ int asm_chain_state(asm_problem *p, double *f, double *chi2);
 int asm_status(asm_problem *p, asm_stats *out);
 
 /* Allocation-free sampling.  The paper has no counterpart: this call exists
- * for callers that cannot allocate device memory themselves -- code that runs
- * while a stream is being captured into a CUDA graph (cudaMalloc is not
- * allowed there), plug-ins whose host application owns every device
- * allocation through its own pool, or loops under a fixed memory budget.
+ * for callers that cannot allocate device memory themselves.  Examples: a
+ * plug-in inside a host application that owns every byte of device memory
+ * through its own pool (a cudaMalloc behind the pool's back breaks its
+ * accounting and fails once the pool holds the memory), and service loops
+ * that run under a fixed memory budget set at start-up, where an allocation
+ * in the loop may fail, block or synchronise the device at an unpredictable
+ * moment.
  * It runs the same sampling as asm_sample (fresh chains, burn_in + sweeps
- * sweeps) and then the device part of asm_average, but its scratch (chain
- * states, residuals, sums and counters) lives in one library-owned static
- * device array of ASM_NOALLOC_SCRATCH_BYTES, which every GPU that loads the
+ * sweeps; the mixed path always refreshes its residuals on the tensor cores)
+ * and then the device part of asm_average, but its scratch (chain states,
+ * residuals, sums and counters) lives in one library-owned static device
+ * array of ASM_NOALLOC_SCRATCH_BYTES (64 MiB), which every GPU that loads the
  * library keeps until the process exits.  The call allocates and frees
  * nothing; a run whose asm_workspace_bytes(p, chains, precision) exceeds the
  * array is rejected with ASM_ERR_TOO_LARGE before any GPU work.
@@ -306,8 +310,8 @@ int asm_status(asm_problem *p, asm_stats *out);
  * shares the array and re-initialises what must start at zero, and the array
  * keeps the last call's contents: calls whose GPU work overlaps (other
  * streams, threads or handles on the same device) race on it and must be
- * serialised by the caller.  Until the next sampling call, asm_chain_state and
- * asm_status of the handle read the array. */
+ * serialised by the caller.  Until the next sampling call, asm_chain_state,
+ * asm_status, asm_mc_error and asm_checkpoint of the handle read the array. */
 #define ASM_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t seed,
                        int precision, double *d_mean_fbar, double *d_sem2_fbar, double *d_m2_fbar,

@@ -1994,9 +1994,11 @@ int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, ui
     if (p->ev_used && drain_events(p) != ASM_OK) return ASM_ERR_CUDA;
     bind_workspace(p, scratch, ASM_NOALLOC_SCRATCH_BYTES, RL, (cudaStream_t)stream);
     p->timing = false;
+    p->refresh_fp64 = false;   // the mixed path refreshes on the tensor cores, whatever ran before
     // counters, sums and residuals are zeroed and the chains re-started here
     rc = start_chains(p, chains, precision, seed, false);
     if (rc != ASM_OK) return rc;
+    p->kept_since = burn_in;   // the kept run starts after this call's burn-in (checkpoints carry it)
     const long long s1 = (long long)burn_in + sweeps;
     p->no_graph = true;   // graph instantiation allocates
     rc = precision == ASM_FP64 ? run_all<double>(p, chains, 0, s1, burn_in) : run_all<float>(p, chains, 0, s1, burn_in);
