@@ -128,128 +128,189 @@ double ora_norm_quantile(double p)
     return x;
 }
 
-/* Right tail: x ~ N(0,1) restricted to [a, b], 0 <= a < b <= inf, by the
- * inverse CDF Q(x) = (1-u) Q(a) + u Q(b).  Returns y = x - a >= 0. */
-static double ora_right_tail(double a, double b, double u, int *capped)
+/* ------------------------------------------------------------------------ */
+/* Truncated normal by the inverse CDF (R1): the draw is the root x of       */
+/* P(a <= X <= x) = u P(a <= X <= b), X ~ N(0,1), found by a bracketing root */
+/* finder on a mass function that keeps its relative accuracy.              */
+/* ------------------------------------------------------------------------ */
+
+/* Mass of N(0,1) on [c, c + y] relative to its density at c, for c >= 0 and
+ * y >= 0 (y = inf allowed):  E(c, y) = int_0^y exp(-c s - s^2/2) ds.
+ * For y (c + y) <= 1: the Taylor series of the Gaussian about c, whose k-th
+ * derivative is (-1)^k He_k(c) phi(c) (probabilists' Hermite polynomials,
+ * He_0 = 1, He_1 = x, He_{k+1} = x He_k - k He_{k-1}), integrated term by
+ * term: E = sum_k (-1)^k He_k(c) y^(k+1) / (k+1)!.
+ * Otherwise the difference of two upper tails, Q(c) - Q(c + y), written with
+ * Q(x) = phi(x) sqrt(pi/2) erfcx(x/sqrt2): the subtracted term is at most
+ * exp(-1/2) of the first one here, so the difference loses no accuracy. */
+static double ora_tail_mass(double c, double y)
 {
-    double y;
-    if (a < 5.0) {
-        double qa = ora_q(a), qb = isinf(b) ? 0.0 : ora_q(b);
-        double q = (1.0 - u) * qa + u * qb;
-        y = -ora_norm_quantile(q) - a;
-    } else {
-        /* log space: log Q(a + y) - log Q(a) = log((1-u) + u r), r = Q(b)/Q(a).
-         * r is formed from erfcx(b)/erfcx(a) and the exact (b-a)(b+a)/2 so that
-         * 1 - r keeps its relative accuracy on narrow intervals; 1 - u is exact
-         * because u lies on the 2^-52 grid. */
-        double exa = ora_erfcx(a / ORA_SQRT2);
-        double r = 0.0, em = -1.0;
-        if (!isinf(b)) {
-            double lr = log(ora_erfcx(b / ORA_SQRT2) / exa) - 0.5 * (b - a) * (b + a);
-            r = exp(lr);
-            em = expm1(lr);
+    if (!(y > 0.0)) return 0.0;
+    if (isfinite(y) && y * (c + y) <= 1.0) {
+        double hm1 = 0.0, h = 1.0;     /* He_{k-1}(c), He_k(c) */
+        double pw = y;                 /* y^(k+1) / (k+1)! */
+        double sum = 0.0;
+        int small = 0;
+        for (int k = 0; k < 200; ++k) {
+            const double term = ((k & 1) ? -h : h) * pw;
+            sum += term;
+            if (fabs(term) <= 1e-18 * fabs(sum)) {
+                if (++small == 2) break;
+            } else {
+                small = 0;
+            }
+            const double hp1 = c * h - k * hm1;
+            hm1 = h;
+            h = hp1;
+            pw *= y / (k + 2);
         }
-        double dt = r < 0.5 ? log((1.0 - u) + u * r) : log1p(u * em);
-        y = -dt / a;
-        int it;
-        for (it = 0; it < 100; ++it) {
-            double exy = ora_erfcx((a + y) / ORA_SQRT2);
-            double g = log(exy / exa) - y * (a + 0.5 * y) - dt;
-            double gp = -ORA_SQRT_2_OVER_PI / exy;
-            double step = g / gp;
-            y -= step;
-            if (fabs(step) <= 1e-14 * (y + 1.0 / a)) break;
-        }
-        if (it == 100 && capped) ++*capped;
+        return sum;
     }
-    if (y < 0.0) y = 0.0;
-    if (y > b - a) y = b - a;
+    const double first = ora_erfcx(c / ORA_SQRT2);
+    const double second = isinf(y) ? 0.0 : ora_erfcx((c + y) / ORA_SQRT2) * exp(-y * (c + 0.5 * y));
+    return 1.25331413731550025121 * (first - second);   /* sqrt(pi/2) */
+}
+
+/* P(z <= X <= c) / phi(0) for 0 <= z <= c (c = inf allowed): decreasing in z. */
+static double ora_upper_mass(double z, double c)
+{
+    return exp(-0.5 * z * z) * ora_tail_mass(z, c - z);
+}
+
+/* The doubles in [lo, hi] (0 <= lo < hi) ordered by their bit patterns: the
+ * pattern halfway between those of lo and hi.  Halving the pattern interval
+ * halves a range of exponents when lo and hi are far apart and the range of
+ * values when they are close, so at most 64 such steps separate any two
+ * non-negative doubles. */
+static double ora_bits_mid(double lo, double hi)
+{
+    uint64_t a, b;
+    memcpy(&a, &lo, 8);
+    memcpy(&b, &hi, 8);
+    uint64_t m = a + (b - a) / 2;
+    double r;
+    memcpy(&r, &m, 8);
+    return r;
+}
+
+/* Root of g(y) = F(y) - target on [lo, hi], 0 <= lo < hi finite, for F
+ * monotone with g(lo) and g(hi) of opposite signs (or zero): regula falsi
+ * with the Illinois modification (Dowell and Jarratt, BIT 11 (1971) 168),
+ * which keeps the root bracketed, and a step of ora_bits_mid whenever a false-
+ * position step leaves more than half of the bracket.  Stops when the bracket
+ * holds no double between its ends; returns the end where g has the sign of
+ * g(hi).  *capped counts solves that hit the iteration cap. */
+typedef double (*ora_mass_fn)(double y, const double *par);
+
+static double ora_bracket_root(ora_mass_fn F, const double *par, double target, double lo, double hi,
+                               int *capped)
+{
+    double glo = F(lo, par) - target, ghi = F(hi, par) - target;
+    if (glo == 0.0) return lo;
+    if (ghi == 0.0 || (glo > 0.0) == (ghi > 0.0)) return hi;
+    const int hi_positive = ghi > 0.0;
+    int side = 0, it;
+    for (it = 0; it < 400; ++it) {
+        if (ora_bits_mid(lo, hi) == lo) break;   /* adjacent doubles */
+        double y = hi - ghi * (hi - lo) / (ghi - glo);
+        if (!(y > lo && y < hi)) y = ora_bits_mid(lo, hi);
+        const double width = hi - lo;
+        const double gy = F(y, par) - target;
+        if (gy == 0.0) return y;
+        if ((gy > 0.0) == hi_positive) {
+            hi = y; ghi = gy;
+            if (side == -1) glo *= 0.5;   /* Illinois: the end kept twice has its value halved */
+            side = -1;
+        } else {
+            lo = y; glo = gy;
+            if (side == 1) ghi *= 0.5;
+            side = 1;
+        }
+        if (hi - lo > 0.5 * width) {      /* slow progress: a bisection step of the bit patterns */
+            const double m = ora_bits_mid(lo, hi);
+            if (m == lo) break;
+            const double gm = F(m, par) - target;
+            if (gm == 0.0) return m;
+            if ((gm > 0.0) == hi_positive) { hi = m; ghi = gm; }
+            else { lo = m; glo = gm; }
+            side = 0;
+        }
+    }
+    if (it == 400 && capped) ++*capped;
+    return hi;
+}
+
+static double ora_tail_mass_fn(double y, const double *par) { return ora_tail_mass(par[0], y); }
+static double ora_upper_mass_fn(double z, const double *par) { return ora_upper_mass(z, par[0]); }
+/* P(c + y <= X <= c + w) / phi(c): the mass above the offset y, decreasing in y */
+static double ora_rest_mass_fn(double y, const double *par)
+{
+    const double c = par[0], w = par[1];
+    return exp(-y * (c + 0.5 * y)) * ora_tail_mass(c + y, w - y);
+}
+
+/* Upper end of a bracket [0, y] for an offset on [c, inf): doubling from the
+ * scale of the density's decay until F passes the target (F increasing) or
+ * drops below it (F decreasing). */
+static double ora_tail_bracket(ora_mass_fn F, const double *par, double target, int increasing)
+{
+    double y = 1.0 / (par[0] + 1.0);
+    for (int k = 0; k < 2100; ++k, y *= 2.0) {
+        const double v = F(y, par);
+        if (increasing ? v >= target : v <= target) break;
+    }
     return y;
 }
 
-/* Gauss-Legendre nodes and weights on [-1, 1] (8 points), from Newton's method
- * on the Legendre polynomial P_8 evaluated by its three-term recurrence. */
-static double ora_gl_x[8], ora_gl_w[8];
-static int ora_gl_ready = 0;
-
-static void ora_gl_init(void)
-{
-    if (ora_gl_ready) return;
-    const int n = 8;
-    for (int i = 0; i < n; ++i) {
-        double x = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = x;
-            for (int k = 2; k <= n; ++k) {
-                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-                p0 = p1;
-                p1 = p2;
-            }
-            dp = n * (x * p1 - p0) / (x * x - 1.0);
-            double dx = p1 / dp;
-            x -= dx;
-            if (fabs(dx) < 1e-17) break;
-        }
-        ora_gl_x[i] = x;
-        ora_gl_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
-    }
-    ora_gl_ready = 1;
-}
-
-/* I(t) = int_0^t exp(-a s - s^2/2) ds, the unnormalised CDF of N(0,1) on
- * [a, a + w] measured from a, by 8-point Gauss-Legendre (relative error ~1e-16
- * while t (|a| + t) <= 1/2). */
-static double ora_narrow_cdf(double a, double t)
-{
-    double acc = 0.0;
-    for (int i = 0; i < 8; ++i) {
-        double s = 0.5 * t * (1.0 + ora_gl_x[i]);
-        acc += ora_gl_w[i] * exp(-a * s - 0.5 * s * s);
-    }
-    return 0.5 * t * acc;
-}
-
-/* Narrow interval [a, a + w] (w (|a| + w) <= 1/2): the inverse CDF
- * I(t) = u I(w) solved by Newton's method from the uniform guess t = u w.
- * Returns the offset t from a with relative accuracy, however small w is. */
-static double ora_narrow(double a, double w, double u, int *capped)
-{
-    double target = u * ora_narrow_cdf(a, w), t = u * w;
-    int it;
-    for (it = 0; it < 60; ++it) {
-        double step = (ora_narrow_cdf(a, t) - target) / exp(-a * t - 0.5 * t * t);
-        t -= step;
-        if (t < 0.0) t = 0.0;
-        if (t > w) t = w;
-        if (fabs(step) <= 4e-16 * t || t == 0.0) break;
-    }
-    if (it == 60 && capped) ++*capped;
-    return t;
-}
-
+/* delta ~ N(mu, sigma^2) restricted to [lo, hi] (lo < hi) by the inverse CDF
+ * at u.  In standard units the interval is [a, b] = [(lo-mu)/sigma,
+ * (hi-mu)/sigma].  The root is always sought from the side whose share of the
+ * mass is the smaller one (u or 1 - u), so that the function solved is steep
+ * where the root lies:
+ *  - a >= 0: the offset y = x - a from the lower end solves E(a, y) = u Z
+ *    (u <= 1/2) or P(a + y <= X <= b) / phi(a) = (1 - u) Z (u > 1/2), with
+ *    Z = E(a, b - a); delta = lo + sigma y.
+ *  - b <= 0: the mirror image, measured down from hi with 1 - u (exact: u lies
+ *    on the 2^-52 grid).
+ *  - a < 0 < b: the mass left of 0 is sqrt(pi/2) erf(|a|/sqrt2).  A root left
+ *    of 0 is x = -z with P(z <= -X <= |a|) = u P(a <= X <= b); a root right of
+ *    0 is x = z with P(z <= X <= b) = (1 - u) P(a <= X <= b).  Both keep z
+ *    accurate near 0 and near the end it is measured from.
+ * Any root of the straddling case lies within 40 of 0 (the targets are at
+ * least 2^-53 of a mass of order one there), which bounds the brackets. */
 static double ora_truncnorm_impl(double mu, double sigma, double lo, double hi, double u,
                                  int *capped)
 {
     if (!(hi > lo)) return lo;
-    double alpha = (lo - mu) / sigma, beta = (hi - mu) / sigma;
-    double wid = (hi - lo) / sigma;     /* interval width in units of sigma */
+    const double a = (lo - mu) / sigma, b = (hi - mu) / sigma;
     double d;
-    if (isfinite(wid) && wid * (fabs(alpha) + wid) <= 0.5) {
-        /* nearly flat over the interval: Gauss-Legendre inverse CDF */
-        d = lo + sigma * ora_narrow(alpha, wid, u, capped);
-    } else if (alpha >= 0.0) {
-        d = lo + sigma * ora_right_tail(alpha, beta, u, capped);
-    } else if (beta <= 0.0) {
-        d = hi - sigma * ora_right_tail(-beta, -alpha, 1.0 - u, capped);
-    } else {
-        double pa = ora_norm_cdf(alpha), pb = ora_norm_cdf(beta);
-        double p = (1.0 - u) * pa + u * pb;
-        double x;
-        if (p <= 0.5) {
-            x = ora_norm_quantile(p);
+    if (a >= 0.0 || b <= 0.0) {
+        const int mirror = a < 0.0;
+        const double c = mirror ? -b : a;
+        const double w = (hi - lo) / sigma;
+        const double uu = mirror ? 1.0 - u : u;
+        const double par[2] = {c, w};
+        const double Z = ora_tail_mass(c, w);
+        double y;
+        if (uu <= 0.5) {
+            const double top = isfinite(w) ? w : ora_tail_bracket(ora_tail_mass_fn, par, uu * Z, 1);
+            y = ora_bracket_root(ora_tail_mass_fn, par, uu * Z, 0.0, top, capped);
         } else {
-            double q = (1.0 - u) * ora_q(alpha) + u * ora_q(beta);
-            x = -ora_norm_quantile(q);
+            const double top = isfinite(w) ? w : ora_tail_bracket(ora_rest_mass_fn, par, (1.0 - uu) * Z, 0);
+            y = ora_bracket_root(ora_rest_mass_fn, par, (1.0 - uu) * Z, 0.0, top, capped);
+        }
+        d = mirror ? hi - sigma * y : lo + sigma * y;
+    } else {
+        const double mass_left = 1.25331413731550025121 * erf(-a / ORA_SQRT2);
+        const double mass_right = 1.25331413731550025121 * erf(b / ORA_SQRT2);
+        const double total = mass_left + mass_right;
+        double x;
+        if (u * total <= mass_left) {
+            const double par[1] = {-a};
+            x = -ora_bracket_root(ora_upper_mass_fn, par, u * total, 0.0, fmin(-a, 40.0), capped);
+        } else {
+            const double par[1] = {b};
+            x = ora_bracket_root(ora_upper_mass_fn, par, (1.0 - u) * total, 0.0, fmin(b, 40.0), capped);
         }
         d = mu + sigma * x;
     }
@@ -260,7 +321,6 @@ static double ora_truncnorm_impl(double mu, double sigma, double lo, double hi, 
 
 double ora_truncnorm(double mu, double sigma, double lo, double hi, double u)
 {
-    ora_gl_init();
     return ora_truncnorm_impl(mu, sigma, lo, hi, u, &(int){0});
 }
 
@@ -733,7 +793,6 @@ int ora_run_ids(const ora_problem *p, int chains, const double *f_start, long sw
 {
     int N = p->N;
     long tot[4] = {0, 0, 0, 0};
-    ora_gl_init();
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #else
