@@ -42,9 +42,6 @@ from paper_1912_01379_gb300 import workloads as W  # noqa: E402
 METRIC = "chain-mode updates/s and ESS/s of <A(omega)>: mixed-prec vs plain FP64, 1 GB300"
 UNIT = "chain-mode updates/s"
 WORKLOAD = "blocked_modes_fermionic_b20_Ntau100_Nomega400_gauss3_8x50_1024chains"
-PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -60,6 +57,7 @@ def _args():
     ap.add_argument("--fp64-sweeps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="heuristic launch shape instead of asm_tune's")
     ap.add_argument("--batch-sweeps", type=int, default=256,
                     help="sweeps of the batching side measurement (0: skip)")
     ap.add_argument("--grid-sweeps", type=int, default=64,
@@ -144,18 +142,49 @@ def _level_sequence(seed, n_sweeps, n_levels, problem_id=0):
 
 
 def _ops_per_level(p):
-    """Algorithmic FP32 lane operations per chain and sweep at every level:
-    6 per element per move (update FMA, clamp, two bound products, two masked
-    min/max) plus 2 M min(M, n_b) for the block's entry and exit projections."""
-    ops = []
+    """Algorithmic work per chain and sweep at every level, as two arrays:
+    pass elements (n_b elements per move, n_b moves per block: update FMA,
+    clamp, bound product and two bound minima per element, counted as 6 FP32
+    lane operations as the method states them, Sec. IV.B) and the FMAs of the
+    block's entry and exit projections (2 M min(M, n_b), Sec. IV.D)."""
+    elems, fmas = [], []
     for starts in p.levels:
         ends = list(starts[1:]) + [p.N]
-        tot = 0
+        e_tot, f_tot = 0, 0
         for s, e in zip(starts, ends):
             n = int(e - s)
-            tot += 6 * n * n + 2 * p.M * min(p.M, n)
-        ops.append(tot)
-    return np.array(ops, dtype=np.float64)
+            e_tot += n * n
+            f_tot += 2 * p.M * min(p.M, n)
+        elems.append(e_tot)
+        fmas.append(f_tot)
+    return np.array(elems, dtype=np.float64), np.array(fmas, dtype=np.float64)
+
+
+OPS_PER_ELEMENT = 6
+
+
+def measured_ceilings(asm):
+    """Rates of the chain kernel's instruction mixes on this GPU
+    (asm_measure_ceiling): the fused pass (elements/s) and the FMA alone, in
+    FP32 and FP64, each with the SM clock seen during its launch."""
+    out = {}
+    for k in ("pass_f32", "pass_f32_smem", "ffma", "fmnmx", "imnmx", "pass_f64", "pass_f64_smem", "dfma",
+              "dmnmx", "i64mnmx"):
+        out[k] = asm.measure_ceiling(k, 40.0)
+    return out
+
+
+def roofline(elems, fmas, kernel_s, ceil, prec):
+    """Achieved and peak algorithmic lane operations per second of the chain
+    kernel: work = 6 per pass element + 1 per projection FMA; the peak is the
+    time the same work takes at the measured rates of the pass mix and of the
+    FMA alone (register operands), i.e. a weighted harmonic mean of the two."""
+    pk, fk = ("pass_f32", "ffma") if prec == "f32" else ("pass_f64", "dfma")
+    ops = OPS_PER_ELEMENT * elems + fmas
+    t_min = elems / ceil[pk]["rate"] + fmas / ceil[fk]["rate"]
+    peak = ops / t_min / 1e12
+    achieved = ops / kernel_s / 1e12 if kernel_s > 0 else None
+    return achieved, peak
 
 
 def _captured_traffic():
@@ -172,14 +201,6 @@ def _captured_traffic():
     except (OSError, ValueError, KeyError):
         pass
     return None
-
-
-def _peaks():
-    try:
-        with open(PEAKS) as fh:
-            return json.load(fh), "measured"
-    except (OSError, ValueError):
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
 def cpu_baseline(p, seconds_target=12.0):
@@ -412,19 +433,21 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     seed_base = 1000
 
+    # launch shape: the autotuner's pick for this workload (set-up, untimed)
+    tuned = gp.tune(chains) if not args.no_tune else None
     # warm-up (untimed), full steps
     for w in range(args.warmup):
         gp.sample(chains, burn, sweeps if w == args.warmup - 1 else max(sweeps // 10, 64), seed_base + w)
     torch.cuda.synchronize()
 
     # timed region: K steps, L2 flushed between steps, CUDA events per step
-    ops_lvl = _ops_per_level(p)
+    elems_lvl, fmas_lvl = _ops_per_level(p)
     clk = ClockSampler(dev)
     clk.start()
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    step_ms, sweep_ms, sweep_launches, other_launches, ops_total = [], 0.0, 0, 0, 0.0
+    step_ms, sweep_ms, sweep_launches, other_launches, elems_total, fmas_total = [], 0.0, 0, 0, 0.0, 0.0
     ess_min = []
     for k in range(args.steps):
         flush.fill_(k & 0xff)
@@ -449,7 +472,8 @@ def main():
             ess = e.cpu().numpy()
         ess_min.append(float(np.nanmin(ess)))
         lv = _level_sequence(seed, burn + sweeps, len(p.levels))
-        ops_total += chains * float(np.sum(ops_lvl[lv]))
+        elems_total += chains * float(np.sum(elems_lvl[lv]))
+        fmas_total += chains * float(np.sum(fmas_lvl[lv]))
     torch.cuda.synchronize()
     t_local = sum(step_ms) / 1e3
     if ws > 1:
@@ -464,11 +488,10 @@ def main():
     ms_per_step = 1e3 * t_max / args.steps
     ess_per_s = float(np.mean(ess_min)) / (ms_per_step / 1e3)
 
-    # dominant kernel roofline: FP32 lane operations (ALU-bound path)
-    peaks, src = _peaks()
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12    # T lane-op/s
-    achieved = ops_total / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
+    # dominant kernel roofline: algorithmic lane operations against the measured
+    # rates of the kernel's own instruction mix (ALU/issue-bound path)
+    ceil = measured_ceilings(asm)
+    achieved, peak = roofline(elems_total, fmas_total, sweep_ms / 1e3, ceil, "f32")
 
     # plain FP64 path, same workload, shorter run (a rate)
     fp64 = None
@@ -478,15 +501,25 @@ def main():
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        seed64, burn64 = seed_base + 1000, f64s // 10
         e0.record(stream)
-        gp.sample(chains, f64s // 10, f64s, seed_base + 1000, precision=asm.ASM_FP64)
+        gp.sample(chains, burn64, f64s, seed64, precision=asm.ASM_FP64, timing=True)
         e1.record(stream)
         e1.synchronize()
         t64 = e0.elapsed_time(e1) / 1e3
+        st64 = gp.status()
         r64 = gp.mc_error()
-        upd64 = chains * (f64s + f64s // 10) * p.N
+        upd64 = chains * (f64s + burn64) * p.N
+        lv64 = _level_sequence(seed64, burn64 + f64s, len(p.levels))
+        a64, pk64 = roofline(chains * float(np.sum(elems_lvl[lv64])), chains * float(np.sum(fmas_lvl[lv64])),
+                             st64["sweep_kernel_ms"] / 1e3, ceil, "f64")
         fp64 = {"updates_per_s": upd64 / t64, "ess_per_s": float(np.nanmin(r64["ess"])) / t64,
-                "sweeps": f64s, "burn_in": f64s // 10}
+                "sweeps": f64s, "burn_in": burn64,
+                "roofline": {"bound": "alu", "achieved": a64, "peak": pk64, "unit": "T lane-op/s",
+                             "frac": a64 / pk64 if a64 else None,
+                             "peak_source": "measured: FP64 pass mix and DFMA (asm_measure_ceiling)",
+                             "kernel": "sweep_kernel<double>",
+                             "avg_launch_ms": st64["sweep_kernel_ms"] / max(st64["timed_launches"], 1)}}
 
     # end to end through the C ABI from host buffers
     e2e = None
@@ -495,13 +528,13 @@ def main():
         d2h = 4 * p.N * 8
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for k in range(max(1, min(args.steps, 2))):
+        nst = max(1, args.steps)
+        for k in range(nst):
             q = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w)
             q.sample(chains, burn, sweeps, seed_base + 200 + k)
             q.average()
             del q
         torch.cuda.synchronize()
-        nst = max(1, min(args.steps, 2))
         te = (time.perf_counter() - t0) / nst
         e2e = {"value": ws * updates_per_step / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": nst}
@@ -531,8 +564,15 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-op/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": _captured_traffic(),
                          "traffic_unit": "DRAM bytes per launch (ncu capture, profiles/)",
-                         "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({src} sm_max_mhz)",
-                         "kernel": "sweep_kernel<float>", "avg_launch_ms": sweep_ms / max(sweep_launches, 1)},
+                         "peak_source": "measured: FP32 pass mix and FFMA on this GPU (asm_measure_ceiling, "
+                                        "register operands), weighted by the workload's pass and projection work",
+                         "kernel": "sweep_kernel<float>", "avg_launch_ms": sweep_ms / max(sweep_launches, 1),
+                         "work": {"pass_elements": elems_total, "projection_fmas": fmas_total,
+                                  "lane_ops_per_element": OPS_PER_ELEMENT}},
+            "ceilings": {k: {"rate": v["rate"], "sm_mhz": v["sm_mhz"]} for k, v in ceil.items()},
+            "launch_shape": {"tuned": tuned, "team_lanes": st["team_lanes"],
+                             "consumers_per_cta": st["consumers_per_cta"], "ctas": st["ctas"],
+                             "ctas_per_sm_budget": st["min_blocks"]},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "batch": batch,

@@ -317,6 +317,29 @@ int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, ui
                        int precision, double *d_mean_fbar, double *d_sem2_fbar, double *d_m2_fbar,
                        void *stream);
 
+/* Measured arithmetic ceilings (no counterpart in the paper: the denominators
+ * of the chain kernel's roofline).  Runs the chosen instruction mix on
+ * register operands (the _SMEM kinds: V and R from shared memory as 16-byte
+ * vectors, as the chain kernel reads them) on every SM at full occupancy with
+ * eight independent streams per thread, growing the loop until one launch
+ * takes about target_ms (0 < target_ms <= 2000), and returns the rate.
+ *   ASM_CEIL_PASS_F32/_F64: elements per second of the fused pass of a move
+ *     (Sec. IV.B): the update f + delta V (FMA), the clamp at 0 (max), the
+ *     bound product x R (multiply) and the signed and unsigned integer minima
+ *     of its bits (the two bound keys).
+ *   ASM_CEIL_FFMA, _FMNMX, _IMNMX, _DFMA, _DMNMX, _I64MNMX: instructions per
+ *     second of one operation alone (min/max kinds: of each minimum).
+ * *sm_mhz (may be NULL) receives the SM clock during the launch, from
+ * clock64() against the global timer; *ms (may be NULL) the launch time.
+ * Allocates a few bytes of device memory and one stream, synchronises.
+ * Returns ASM_ERR_ARG for an unknown kind or target. */
+enum {
+    ASM_CEIL_PASS_F32 = 0, ASM_CEIL_PASS_F32_SMEM = 1, ASM_CEIL_FFMA = 2, ASM_CEIL_FMNMX = 3,
+    ASM_CEIL_IMNMX = 4, ASM_CEIL_PASS_F64 = 5, ASM_CEIL_PASS_F64_SMEM = 6, ASM_CEIL_DFMA = 7,
+    ASM_CEIL_DMNMX = 8, ASM_CEIL_I64MNMX = 9, ASM_CEIL_KINDS = 10
+};
+int asm_measure_ceiling(int kind, double target_ms, double *ops_per_s, double *sm_mhz, double *ms);
+
 /* Identities that key the random numbers (Philox counter words): problem_id
  * (default 0) and the global id of local chain 0 (default 0).  Chains are
  * independent and keyed by their global id, so shards of one run placed on

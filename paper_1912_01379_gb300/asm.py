@@ -56,7 +56,10 @@ class asm_stats(ct.Structure):
 EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",
            "asm_status", "asm_destroy", "asm_error_string", "asm_sample_noalloc", "asm_set_stream_ids",
            "asm_checkpoint", "asm_restore", "asm_backward", "asm_setup_batch", "asm_problem_count",
-           "asm_average_at", "asm_tune", "asm_partition_hierarchy", "asm_mc_error"]
+           "asm_average_at", "asm_tune", "asm_partition_hierarchy", "asm_mc_error", "asm_measure_ceiling"]
+# instruction mixes of asm_measure_ceiling
+CEILING_KINDS = {"pass_f32": 0, "pass_f32_smem": 1, "ffma": 2, "fmnmx": 3, "imnmx": 4, "pass_f64": 5,
+                 "pass_f64_smem": 6, "dfma": 7, "dmnmx": 8, "i64mnmx": 9}
 ASM_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
@@ -118,6 +121,8 @@ def load(build_if_missing: bool = True):
     L.asm_partition_hierarchy.restype = ct.c_int
     L.asm_mc_error.argtypes = [ct.c_void_p, ct.c_int, _dp, _dp, _dp, _ip]
     L.asm_mc_error.restype = ct.c_int
+    L.asm_measure_ceiling.argtypes = [ct.c_int, ct.c_double, _dp, _dp, _dp]
+    L.asm_measure_ceiling.restype = ct.c_int
     _lib = L
     return L
 
@@ -139,6 +144,17 @@ def partition_hierarchy(N):
         out.append(bs[o:o + nb[l]].copy())
         o += nb[l]
     return out
+
+
+def measure_ceiling(kind, target_ms=30.0):
+    """asm_measure_ceiling: measured rate of one instruction mix on the current
+    GPU (elements/s for the pass kinds, instructions/s otherwise), with the SM
+    clock seen during the launch (MHz) and the launch time (ms)."""
+    _require_cuda()
+    rate, mhz, ms = ct.c_double(0), ct.c_double(0), ct.c_double(0)
+    _check(load().asm_measure_ceiling(CEILING_KINDS[kind], float(target_ms), ct.byref(rate), ct.byref(mhz),
+                                      ct.byref(ms)), "asm_measure_ceiling")
+    return {"rate": rate.value, "sm_mhz": mhz.value, "ms": ms.value}
 
 
 class ASMError(RuntimeError):

@@ -33,11 +33,27 @@ def test_level_schedule_matches_the_oracle(seed, n_levels, problem_id):
 
 def test_ops_per_level_adds_blocks():
     """Block work adds over the blocks of a level: the whole grid as one block
-    costs more than the same grid cut in two (n^2 per block), and a level of
-    one-point blocks costs 6 N + 2 M N."""
+    has more pass elements than the same grid cut in two (n^2 per block), and a
+    level of one-point blocks has N pass elements and 2 M N projection FMAs."""
     class P:
         M, N = 20, 60
         levels = [np.array([0]), np.array([0, 30]), np.arange(60)]
-    ops = bench._ops_per_level(P)
-    assert ops[0] > ops[1] > 0
-    assert ops[2] == 6 * 60 + 2 * 20 * 60
+    elems, fmas = bench._ops_per_level(P)
+    assert elems[0] > elems[1] > 0
+    assert elems[0] == 60 * 60 and elems[1] == 2 * 30 * 30
+    assert elems[2] == 60 and fmas[2] == 2 * 20 * 60
+    assert fmas[0] == 2 * 20 * 20 and fmas[1] == 2 * (2 * 20 * 20)
+
+
+def test_roofline_peak_is_the_weighted_harmonic_mean():
+    """The peak is the rate of the same work at the measured rates: all-pass
+    work peaks at 6 x the pass rate, all-FMA work at the FMA rate, and a mix
+    lies between them."""
+    ceil = {"pass_f32": {"rate": 1e12}, "ffma": {"rate": 3e13}}
+    a, pk = bench.roofline(np.float64(1e9), np.float64(0.0), 1.0, ceil, "f32")
+    assert pk == pytest.approx(6e12 / 1e12) and a == pytest.approx(6e9 / 1e12)
+    _, pk = bench.roofline(np.float64(0.0), np.float64(1e9), 1.0, ceil, "f32")
+    assert pk == pytest.approx(3e13 / 1e12)
+    _, pk = bench.roofline(np.float64(1e9), np.float64(1e9), 1.0, ceil, "f32")
+    assert 6.0 < pk < 30.0
+    assert pk == pytest.approx(7e9 / (1e9 / 1e12 + 1e9 / 3e13) / 1e12)
