@@ -325,6 +325,70 @@ double ora_truncnorm(double mu, double sigma, double lo, double hi, double u)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Robert's rejection sampler (C. P. Robert, "Simulation of truncated normal */
+/* variables", Statistics and Computing 5 (1995) 121-125): an independent   */
+/* route to the same distribution, used only to cross-check the inverse CDF */
+/* above in distribution.  Uniforms come from Philox4x64-10 with key        */
+/* {seed, 0x526f62657274} and counter {k/4, stream, 0, 0}.                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t key[2], stream, k, w[4];
+} ora_ustream;
+
+static double ora_next_u(ora_ustream *s)
+{
+    if ((s->k & 3) == 0) {
+        const uint64_t ctr[4] = {s->k >> 2, s->stream, 0, 0};
+        ora_philox4x64_10(ctr, s->key, s->w);
+    }
+    return ora_u01(s->w[s->k++ & 3]);
+}
+
+/* One draw of X ~ N(0,1) restricted to [a, b] (a < b, either may be infinite).
+ * Proposals (Robert 1995, Sec. 2): for a >= 0, the exponential translated to a
+ * with the optimal rate l = (a + sqrt(a^2 + 4))/2, accepted with probability
+ * exp(-(z - l)^2/2) and rejected beyond b, unless the interval is short
+ * enough that the uniform proposal on [a, b] (accepted with probability
+ * exp((a^2 - z^2)/2)) is the better one; for a < 0 < b, the uniform proposal
+ * (accepted with exp(-z^2/2)) on intervals shorter than sqrt(2 pi), else
+ * N(0,1) itself by Box-Muller, rejected outside [a, b]; b <= 0 by symmetry. */
+static double ora_robert_draw(double a, double b, ora_ustream *s, long *tries)
+{
+    if (b <= 0.0) return -ora_robert_draw(-b, -a, s, tries);
+    for (;;) {
+        ++*tries;
+        if (a >= 0.0) {
+            const double r = sqrt(a * a + 4.0);
+            const double l = 0.5 * (a + r);
+            const double b_switch = a + 2.0 / (a + r) * exp(0.25 * (a * a - a * r) + 0.5);
+            if (b <= b_switch) {
+                const double z = a + (b - a) * ora_next_u(s);
+                if (ora_next_u(s) <= exp(0.5 * (a - z) * (a + z))) return z;
+            } else {
+                const double z = a - log(ora_next_u(s)) / l;
+                const double acc = exp(-0.5 * (z - l) * (z - l));
+                if (ora_next_u(s) <= acc && z <= b) return z;
+            }
+        } else if (b - a < 2.50662827463100050242) {   /* sqrt(2 pi) */
+            const double z = a + (b - a) * ora_next_u(s);
+            if (ora_next_u(s) <= exp(-0.5 * z * z)) return z;
+        } else {
+            const double u1 = ora_next_u(s), u2 = ora_next_u(s);
+            const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+            if (z >= a && z <= b) return z;
+        }
+    }
+}
+
+long ora_truncnorm_robert(double a, double b, uint64_t seed, uint64_t stream, int n, double *out)
+{
+    ora_ustream s = {{seed, 0x526f62657274ULL}, stream, 0, {0, 0, 0, 0}};
+    long tries = 0;
+    for (int i = 0; i < n; ++i) out[i] = ora_robert_draw(a, b, &s, &tries);
+    return tries;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Linear algebra                                                           */
 /* ------------------------------------------------------------------------ */
 int ora_cholesky(int n, const double *C, double *L)
@@ -442,6 +506,7 @@ struct ora_problem {
     ora_block *blk;
     double *Kt, *gt;     /* whitened kernel (M x N row-major) and data */
     double *prior_am1;   /* a_n - 1 of the gamma prior prod f_n^(a_n - 1) (Eq. compat), NULL: flat */
+    int flat_exp;        /* R2: sign-changing modes with d <= d_1 max(M,n) 2^-flat_exp are flat */
 };
 
 void ora_free(ora_problem *p)
@@ -478,7 +543,7 @@ static int ora_block_svd(const ora_problem *p, ora_block *b)
      * interval Delta: such a mode is sampled flat when its vector changes sign
      * (so that the interval is finite) and keeps its Gaussian otherwise. */
     const double dmax = (double)(M > n ? M : n);
-    const double thr0 = s[0] * dmax * 0x1p-52, thr = s[0] * dmax * 0x1p-40;
+    const double thr0 = s[0] * dmax * 0x1p-52, thr = s[0] * dmax * ldexp(1.0, -p->flat_exp);
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) b->V[(size_t)j * n + i] = V[(size_t)i * n + j];
     for (int j = 0; j < n; ++j) {
@@ -502,16 +567,18 @@ static int ora_block_svd(const ora_problem *p, ora_block *b)
     return 0;
 }
 
-ora_problem *ora_setup(int M, int N, const double *K, const double *G, const double *C,
-                       int n_levels, const int *level_nblocks, const int *block_start, int *err)
+ora_problem *ora_setup_ex(int M, int N, const double *K, const double *G, const double *C,
+                          int n_levels, const int *level_nblocks, const int *block_start, int flat_exp,
+                          int *err)
 {
     *err = 0;
-    if (M < 1 || N < 1 || n_levels < 1) { *err = -1; return NULL; }
+    if (M < 1 || N < 1 || n_levels < 1 || flat_exp < 1 || flat_exp > 52) { *err = -1; return NULL; }
     for (long i = 0; i < (long)M * N; ++i) if (!isfinite(K[i])) { *err = -3; return NULL; }
     for (int i = 0; i < M; ++i) if (!isfinite(G[i])) { *err = -3; return NULL; }
     for (long i = 0; i < (long)M * M; ++i) if (!isfinite(C[i])) { *err = -3; return NULL; }
     ora_problem *p = (ora_problem *)calloc(1, sizeof(ora_problem));
     p->M = M; p->N = N; p->n_levels = n_levels;
+    p->flat_exp = flat_exp;
     p->level_nblocks = (int *)malloc(sizeof(int) * n_levels);
     p->level_first = (int *)malloc(sizeof(int) * n_levels);
     int nb = 0;
@@ -553,6 +620,12 @@ ora_problem *ora_setup(int M, int N, const double *K, const double *G, const dou
         if (rc != 0) { *err = rc == -4 ? -4 : -1; ora_free(p); return NULL; }
     }
     return p;
+}
+
+ora_problem *ora_setup(int M, int N, const double *K, const double *G, const double *C,
+                       int n_levels, const int *level_nblocks, const int *block_start, int *err)
+{
+    return ora_setup_ex(M, N, K, G, C, n_levels, level_nblocks, block_start, 40, err);
 }
 
 void ora_sizes(const ora_problem *p, long *n_d, long *n_V, long *n_U)

@@ -31,6 +31,12 @@ double ora_log_q(double x);                    /* log Q(x) for x >= 0 */
 /* One draw of N(mu, sigma^2) truncated to [lo, hi] by the inverse CDF at u. */
 double ora_truncnorm(double mu, double sigma, double lo, double hi, double u);
 
+/* n draws of N(0,1) restricted to [a, b] by Robert's rejection sampler
+ * (Statistics and Computing 5 (1995) 121), with uniforms from Philox4x64-10
+ * keyed by (seed, stream).  Independent of ora_truncnorm: a distributional
+ * cross-check.  Returns the number of proposals made. */
+long ora_truncnorm_robert(double a, double b, uint64_t seed, uint64_t stream, int n, double *out);
+
 /* Cholesky C = L L^T of an n x n SPD matrix (row-major). 0 on success. */
 int ora_cholesky(int n, const double *C, double *L);
 
@@ -52,6 +58,12 @@ typedef struct ora_problem ora_problem;
 ora_problem *ora_setup(int M, int N, const double *K, const double *G, const double *C,
                        int n_levels, const int *level_nblocks, const int *block_start,
                        int *err);
+/* Same with the exponent of reading R2 (zero modes) given: sign-changing modes
+ * with d <= d_1 max(M, n) 2^-flat_exp are sampled flat (ora_setup: 40; 52
+ * leaves only the numerically zero modes flat).  1 <= flat_exp <= 52. */
+ora_problem *ora_setup_ex(int M, int N, const double *K, const double *G, const double *C,
+                          int n_levels, const int *level_nblocks, const int *block_start, int flat_exp,
+                          int *err);
 void ora_free(ora_problem *p);
 
 /* Sizes of the exported factors: total entries of d, V and U over all blocks. */

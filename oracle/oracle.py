@@ -46,12 +46,16 @@ def lib():
             getattr(L, name).restype = ct.c_double
         L.ora_truncnorm.argtypes = [ct.c_double] * 5
         L.ora_truncnorm.restype = ct.c_double
+        L.ora_truncnorm_robert.argtypes = [ct.c_double, ct.c_double, ct.c_uint64, ct.c_uint64, ct.c_int, _dp]
+        L.ora_truncnorm_robert.restype = ct.c_long
         L.ora_cholesky.argtypes = [ct.c_int, _dp, _dp]
         L.ora_cholesky.restype = ct.c_int
         L.ora_jacobi_svd.argtypes = [ct.c_int, ct.c_int, _dp, _dp, _dp, _dp]
         L.ora_jacobi_svd.restype = ct.c_int
         L.ora_setup.argtypes = [ct.c_int, ct.c_int, _dp, _dp, _dp, ct.c_int, _ip, _ip, _ip]
         L.ora_setup.restype = ct.c_void_p
+        L.ora_setup_ex.argtypes = [ct.c_int, ct.c_int, _dp, _dp, _dp, ct.c_int, _ip, _ip, ct.c_int, _ip]
+        L.ora_setup_ex.restype = ct.c_void_p
         L.ora_free.argtypes = [ct.c_void_p]
         L.ora_sizes.argtypes = [ct.c_void_p, _lp, _lp, _lp]
         L.ora_export.argtypes = [ct.c_void_p, _dp, _dp, _dp, _dp, _dp]
@@ -109,6 +113,14 @@ def truncnorm(mu, sigma, lo, hi, u):
     return lib().ora_truncnorm(float(mu), float(sigma), float(lo), float(hi), float(u))
 
 
+def truncnorm_robert(a, b, n, seed=1, stream=0):
+    """n draws of N(0,1) on [a, b] by Robert's (1995) rejection sampler and
+    the number of proposals it made."""
+    out = np.zeros(n)
+    tries = lib().ora_truncnorm_robert(float(a), float(b), ct.c_uint64(seed), ct.c_uint64(stream), n, _d(out))
+    return out, tries
+
+
 def cholesky(C):
     C = np.ascontiguousarray(C, dtype=np.float64)
     L = np.zeros_like(C)
@@ -144,7 +156,7 @@ class Decomposition:
 class OracleProblem:
     ERRORS = {-1: "shape", -2: "not SPD", -3: "non-finite", -4: "improper zero mode"}
 
-    def __init__(self, K, G, C, levels, prior_shape=None):
+    def __init__(self, K, G, C, levels, prior_shape=None, flat_exp=40):
         K = np.ascontiguousarray(K, dtype=np.float64)
         G = np.ascontiguousarray(G, dtype=np.float64)
         C = np.ascontiguousarray(C, dtype=np.float64)
@@ -153,8 +165,8 @@ class OracleProblem:
         nb = np.array([len(l) for l in self.levels], dtype=np.int32)
         bs = np.concatenate(self.levels).astype(np.int32)
         err = ct.c_int(0)
-        self._h = lib().ora_setup(self.M, self.N, _d(K), _d(G), _d(C), len(self.levels),
-                                  nb.ctypes.data_as(_ip), bs.ctypes.data_as(_ip), ct.byref(err))
+        self._h = lib().ora_setup_ex(self.M, self.N, _d(K), _d(G), _d(C), len(self.levels),
+                                     nb.ctypes.data_as(_ip), bs.ctypes.data_as(_ip), int(flat_exp), ct.byref(err))
         if not self._h:
             raise ValueError(f"oracle setup failed: {self.ERRORS.get(err.value, err.value)}")
         self.err = err.value
