@@ -66,8 +66,10 @@ def _args():
                     help="sweeps per grid of the paper-test-case side measurement (0: skip)")
     ap.add_argument("--hierarchy-sweeps", type=int, default=3000,
                     help="sweeps per partition scheme of the hierarchy side measurement (0: skip)")
-    ap.add_argument("--diff-sweeps", type=int, default=0,
+    ap.add_argument("--diff-sweeps", type=int, default=2000,
                     help="kept sweeps per run of the differentiation side measurement (0: skip)")
+    ap.add_argument("--diff-budget-s", type=float, default=90.0,
+                    help="time budget of the differentiation side measurement (seconds)")
     return ap.parse_args()
 
 
@@ -321,33 +323,41 @@ def diff_side(args, asm, torch, stream):
     8-parameter Gaussian-mixture density on [-6, 6], beta = 16, noise 1e-4,
     4096 chains, global level plus 8 blocks of 25): mixed-precision sampling
     with the snapshot moments, then the vector-Jacobian products of <A> with
-    respect to G and the 8 grid parameters (asm_backward).  Four runs with
-    different seeds give the standard error of each product."""
+    respect to G and the 8 grid parameters (asm_backward).  Independent runs
+    (seeds) are added until the relative standard error of the mean of each
+    product is at most 2.5e-4 (the workload's stopping rule), or the time
+    budget is spent."""
     p = W.theta_problem()
-    chains, burn, sweeps, runs = p.chains, 500, args.diff_sweeps, 4
+    chains, burn, sweeps = p.chains, 500, args.diff_sweeps
     gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w, dK_dtheta=p.extra["dK_dtheta"],
                      dw_dtheta=p.extra["dw_dtheta"])
     v = np.random.default_rng(7).standard_normal(p.N)
     t_sample, t_back, gG, gT = [], [], [], []
-    for r in range(runs):
-        t_sample.append(_timed(torch, stream, lambda: gp.sample(chains, burn, sweeps, 100 + r,
-                                                                precision=asm.ASM_MIXED, moments=True)))
-        t0 = time.perf_counter()
-        g, t = gp.backward(v)
-        t_back.append(time.perf_counter() - t0)
-        gG.append(g)
-        gT.append(t)
-    gG, gT = np.array(gG), np.array(gT)
 
     def rel_sem(x):
-        return float(np.linalg.norm(x.std(axis=0, ddof=1) / np.sqrt(runs)) / np.linalg.norm(x.mean(axis=0)))
+        x = np.array(x)
+        return float(np.linalg.norm(x.std(axis=0, ddof=1) / np.sqrt(len(x))) / np.linalg.norm(x.mean(axis=0)))
 
+    target, t0 = 2.5e-4, time.perf_counter()
+    while True:
+        r = len(gG)
+        t_sample.append(_timed(torch, stream, lambda: gp.sample(chains, burn, sweeps, 100 + r,
+                                                                precision=asm.ASM_MIXED, moments=True)))
+        tb = time.perf_counter()
+        g, t = gp.backward(v)
+        t_back.append(time.perf_counter() - tb)
+        gG.append(g)
+        gT.append(t)
+        done = len(gG) >= 3 and rel_sem(gG) <= target and rel_sem(gT) <= target
+        if done or time.perf_counter() - t0 > args.diff_budget_s:
+            break
     return {"workload": "differentiation_b16_Ntau64_Nomega200_theta8_4096chains", "chains": chains,
-            "burn_in": burn, "sweeps": sweeps, "runs": runs,
+            "burn_in": burn, "sweeps": sweeps, "runs": len(gG), "target_rel_sem": target,
+            "converged": bool(done), "seconds": time.perf_counter() - t0,
             "updates_per_s": chains * (burn + sweeps) * p.N / float(np.mean(t_sample)),
             "backward_ms": 1e3 * float(np.mean(t_back)),
             "grad_G_rel_sem": rel_sem(gG), "grad_theta_rel_sem": rel_sem(gT),
-            "grad_theta": gT.mean(axis=0).tolist()}
+            "grad_theta": np.mean(gT, axis=0).tolist()}
 
 
 def paper_side(args, asm, torch, stream):

@@ -507,6 +507,7 @@ struct ora_problem {
     double *Kt, *gt;     /* whitened kernel (M x N row-major) and data */
     double *prior_am1;   /* a_n - 1 of the gamma prior prod f_n^(a_n - 1) (Eq. compat), NULL: flat */
     int flat_exp;        /* R2: sign-changing modes with d <= d_1 max(M,n) 2^-flat_exp are flat */
+    int mu_jitter;       /* test of rounding sensitivity: every conditional mean moved by one ulp */
 };
 
 void ora_free(ora_problem *p)
@@ -628,6 +629,8 @@ ora_problem *ora_setup(int M, int N, const double *K, const double *G, const dou
     return ora_setup_ex(M, N, K, G, C, n_levels, level_nblocks, block_start, 40, err);
 }
 
+void ora_set_mu_jitter(ora_problem *p, int on) { p->mu_jitter = on ? 1 : 0; }
+
 void ora_sizes(const ora_problem *p, long *n_d, long *n_V, long *n_U)
 {
     long a = 0, b = 0, c = 0;
@@ -678,23 +681,33 @@ double ora_chi2(const ora_problem *p, const double *f)
 }
 
 /* Data seen by block b: h_b = U_b^T (g~ - sum_{blocks b' != b} K~_{b'} f_{b'})
- * (Sec. IV.D: the contribution of the other blocks). */
+ * (Sec. IV.D: the contribution of the other blocks).  habs (may be NULL)
+ * receives sum_m |U_jm| (|g~_m| + sum_{n not in b} |K~_mn f_n|), the size of
+ * the terms whose roundings h_j carries. */
 static void ora_block_h(const ora_problem *p, const ora_block *b, const double *f, double *gp,
-                        double *h)
+                        double *h, double *habs)
 {
+    double *gabs = habs ? (double *)malloc(sizeof(double) * p->M) : NULL;
     for (int i = 0; i < p->M; ++i) {
-        double t = p->gt[i];
+        double t = p->gt[i], ta = fabs(p->gt[i]);
         for (int j = 0; j < p->N; ++j) {
             if (j >= b->start && j < b->start + b->n) continue;
             t -= p->Kt[(size_t)i * p->N + j] * f[j];
+            ta += fabs(p->Kt[(size_t)i * p->N + j] * f[j]);
         }
         gp[i] = t;
+        if (gabs) gabs[i] = ta;
     }
     for (int j = 0; j < b->np; ++j) {
-        double t = 0.0;
-        for (int i = 0; i < p->M; ++i) t += b->U[(size_t)j * p->M + i] * gp[i];
+        double t = 0.0, ta = 0.0;
+        for (int i = 0; i < p->M; ++i) {
+            t += b->U[(size_t)j * p->M + i] * gp[i];
+            if (gabs) ta += fabs(b->U[(size_t)j * p->M + i]) * gabs[i];
+        }
         h[j] = t;
+        if (habs) habs[j] = ta;
     }
+    free(gabs);
 }
 
 /* Interval of delta = e_j' - e_j that keeps f + delta V_j >= 0 (Eq. modeLimits, R3). */
@@ -718,17 +731,23 @@ static void ora_bounds(const ora_block *b, int j, const double *f, double *lo, d
 /* Conditional of mode j of block b given the rest (Sec. IV.B-C):
  * e_j' ~ N(h_j/d_j, 1/d_j^2), so delta ~ N(h_j/d_j - e_j, 1/d_j^2). */
 static void ora_mode_conditional(const ora_block *b, int j, const double *f, const double *h,
-                                 double *mu, double *sigma)
+                                 const double *habs, double *mu, double *sigma, double *mu_scale)
 {
     const double *v = b->V + (size_t)j * b->n;
-    double e = 0.0;
-    for (int i = 0; i < b->n; ++i) e += v[i] * f[b->start + i];
+    double e = 0.0, ea = 0.0;
+    for (int i = 0; i < b->n; ++i) {
+        e += v[i] * f[b->start + i];
+        ea += fabs(v[i] * f[b->start + i]);
+    }
     if (b->d[j] > 0.0) {
         *mu = h[j] / b->d[j] - e;
         *sigma = 1.0 / b->d[j];
+        /* the size of every term rounded on the way to mu */
+        if (mu_scale) *mu_scale = (habs ? habs[j] : fabs(h[j])) / b->d[j] + ea;
     } else {
         *mu = 0.0;
         *sigma = 0.0;
+        if (mu_scale) *mu_scale = 0.0;
     }
 }
 
@@ -740,8 +759,8 @@ int ora_conditional(const ora_problem *p, int level, int block, int j, const dou
     if (j < 0 || j >= b->n) return -1;
     double *gp = (double *)malloc(sizeof(double) * p->M);
     double *h = (double *)malloc(sizeof(double) * (b->np > 0 ? b->np : 1));
-    ora_block_h(p, b, f, gp, h);
-    ora_mode_conditional(b, j, f, h, mu, sigma);
+    ora_block_h(p, b, f, gp, h, NULL);
+    ora_mode_conditional(b, j, f, h, NULL, mu, sigma, NULL);
     ora_bounds(b, j, f, lo, hi);
     free(gp); free(h);
     return 0;
@@ -796,6 +815,7 @@ static void ora_chain(const ora_problem *p, uint64_t q, double *f, long sweep0, 
     int M = p->M, N = p->N;
     double *gp = (double *)malloc(sizeof(double) * M);
     double *h = (double *)malloc(sizeof(double) * (M > 0 ? M : 1));
+    double *habs = p->mu_jitter ? (double *)malloc(sizeof(double) * (M > 0 ? M : 1)) : NULL;
     const uint64_t key[2] = {seed, 0};
     long viol = 0, degen = 0, flat = 0;
     int capped = 0;
@@ -807,15 +827,17 @@ static void ora_chain(const ora_problem *p, uint64_t q, double *f, long sweep0, 
         if (level >= p->n_levels) level = p->n_levels - 1;
         for (int bi = 0; bi < p->level_nblocks[level]; ++bi) {
             const ora_block *b = &p->blk[p->level_first[level] + bi];
-            ora_block_h(p, b, f, gp, h);
+            ora_block_h(p, b, f, gp, h, habs);
             for (int j = 0; j < b->n; ++j) {
                 long t = b->start + j;
                 uint64_t ctr[4] = {(uint64_t)t >> 2, (uint64_t)s, (uint64_t)q, problem_id};
                 ora_philox4x64_10(ctr, key, w);
                 double u = ora_u01(w[t & 3]);
-                double mu, sigma, lo, hi, delta;
-                ora_mode_conditional(b, j, f, h, &mu, &sigma);
+                double mu, sigma, lo, hi, delta, mu_scale;
+                ora_mode_conditional(b, j, f, h, habs, &mu, &sigma, &mu_scale);
                 ora_bounds(b, j, f, &lo, &hi);
+                if (p->mu_jitter && sigma > 0.0)   /* a rounding of the terms of mu, up or down by a bit of the move's word */
+                    mu += ((w[t & 3] & 2) ? 1.0 : -1.0) * 0x1p-52 * mu_scale;
                 if (!(hi > lo)) {
                     delta = 0.0;
                     ++degen;
@@ -856,7 +878,7 @@ static void ora_chain(const ora_problem *p, uint64_t q, double *f, long sweep0, 
     if (stats) {
         stats[0] = viol; stats[1] = degen; stats[2] = flat; stats[3] = capped;
     }
-    free(gp); free(h);
+    free(gp); free(h); free(habs);
 }
 
 int ora_run_ids(const ora_problem *p, int chains, const double *f_start, long sweep0,

@@ -66,6 +66,17 @@ ora_problem *ora_setup_ex(int M, int N, const double *K, const double *G, const 
                           int *err);
 void ora_free(ora_problem *p);
 
+/* Rounding-sensitivity probe (tests only): with `on`, every Gaussian move's
+ * conditional mean mu = h_j/d_j - e_j (Sec. IV.B) is moved by one rounding of
+ * the terms it is summed from, 2^-52 (sum_m |U_jm| (|g~_m| + sum_n |K~_mn f_n|)
+ * / d_j + sum_i |V_ji f_i|), up or down by bit 1 of the move's Philox word,
+ * before the draw.  Two correct FP64
+ * implementations of the sampler (e.g. one tracking the residual
+ * incrementally, one recomputing the block's data from scratch) differ at
+ * least by such roundings, so the sweeps over which the probe stays close to
+ * the plain run bound any step-by-step comparison. */
+void ora_set_mu_jitter(ora_problem *p, int on);
+
 /* Sizes of the exported factors: total entries of d, V and U over all blocks. */
 void ora_sizes(const ora_problem *p, long *n_d, long *n_V, long *n_U);
 

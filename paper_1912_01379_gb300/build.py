@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libasm_gb300.so")
 UNITS = ["asm_lib.cu", "asm_sweep_f32.cu", "asm_sweep_f32_m2.cu", "asm_sweep_f32_prior.cu", "asm_sweep_f64.cu",
-         "asm_sweep_f64_m2.cu", "asm_sweep_f64_prior.cu", "asm_refresh_tc.cu", "asm_ceiling.cu"]
+         "asm_sweep_f64_m2.cu", "asm_sweep_f64_prior.cu", "asm_refresh_tc.cu", "asm_ceiling.cu", "asm_moments.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
          "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

@@ -27,7 +27,8 @@ struct BlockDesc {
     long long offU;  // Ut: np x M (mode-major); Um: M x np (grid-major)
     long long offRec;  // move records of the block: n records of recstride elements
     int recstride;     // elements per record (2 rs + 16)
-    int pad_;
+    int usr;           // row stride of the staging copy of U (odd: conflict-free column reads)
+    long long offUs;   // staging copy of U: np rows of usr elements, 16-byte aligned
 };
 
 // Device-side problem data in one precision T.
@@ -36,8 +37,9 @@ struct ProblemData {
     const T *V, *R;          // mode rows V and R = -1/V (NaN where V is left out of the bounds)
     const T *d, *invd;       // singular values and their reciprocals (0 for zero modes)
     const T *meta;           // per mode, 16 bytes: {d, 1/d} (FP32: {d, 1/d, 0, 0})
-    const T *rec;            // per move j: {V_j, R_{j+1} (rs each), d_j, 1/d_j}
+    const T *rec;            // per move j: {V_j, R_{j+1} (rs each), d_j, 1/d_j, |K~_b V_j|}
     const T *Ut, *Um;        // U in two layouts
+    const T *Us;             // U mode-major with odd row stride, copied to shared memory per block visit
 };
 
 struct Counters {            // device counters, first bytes of the workspace
@@ -76,6 +78,10 @@ struct SweepParams {
     // the tensor-core refresh of the mixed path
     const float *Khi, *Klo;
     int ldK;
+    // reference state of the tensor-core refresh: the mean chain state fref (N,
+    // FP32) and r_ref = g~ - K~ fref (M, FP64); the product is taken of f - fref
+    float *fref;
+    double *rref;
     // gamma prior: a_n - 1 per grid point (nullptr: flat)
     const T *prior_am1;
 };
@@ -98,6 +104,11 @@ struct LaunchShape {
     int prior;                        // 1: kernels with the gamma prior's acceptance step
     int wait_limit;                   // polls before a bounded mbarrier wait gives up
     int stall;                        // test of the failure path: the producer issues no records
+    // U of the visited block in shared memory (two stages filled by the producer with
+    // one bulk copy per block visit; 0: the projections read U from global memory)
+    int ubytes;                       // bytes per stage (blocks whose U is larger read global memory)
+    int off_ubuf;                     // byte offset of the two stages
+    int off_ubar;                     // byte offset of their full[2] and empty[2] barriers
 };
 
 // Per-launch control block in device memory: the work queue and the launch's
@@ -141,6 +152,24 @@ int refresh_tc_bn(int M);                  // MMA N of a problem's M_tau tiles
 size_t refresh_tc_smem(int max_bn);        // dynamic shared memory of one CTA
 constexpr int kRefreshTcLdK = 32;          // ldK is a multiple of this (one k-tile)
 cudaError_t launch_split_k(const double *KtT, int M, int N, int ldK, float *Khi, float *Klo, cudaStream_t s);
+// Reference state of every problem's tensor-core refresh (one CTA per problem).
+cudaError_t launch_refresh_ref(const SweepParams<float> *probs, int n_problems, int chains, cudaStream_t s);
+// Contractions of the backward pass (asm_moments.cu).  D: chains x ldD snapshot
+// (centred); Sff (N x N, FP64) += D^T D; Y (chains x PM) = D Kth^T with Kth
+// PM x N row-major (the whitened dK/dtheta of all parameters); Sq (chains x P)
+// = the scores r~_q . (Y_q,p + kshift_p); y = L^{-T} K~ u for the G-product.
+cudaError_t launch_gram(const float *D, int ldD, int chains, int N, double *Sff, cudaStream_t s);
+cudaError_t launch_gram(const double *D, int ldD, int chains, int N, double *Sff, cudaStream_t s);
+cudaError_t launch_kth_product(const float *D, int ldD, int chains, int N, const float *Kth, int PM, float *Y,
+                               cudaStream_t s);
+cudaError_t launch_kth_product(const double *D, int ldD, int chains, int N, const double *Kth, int PM, double *Y,
+                               cudaStream_t s);
+cudaError_t launch_scores(const float *R, int ldR, const float *Y, const double *kshift, int M, int chains, int P,
+                          double *Sq, cudaStream_t s);
+cudaError_t launch_scores(const double *R, int ldR, const double *Y, const double *kshift, int M, int chains, int P,
+                          double *Sq, cudaStream_t s);
+cudaError_t launch_vjp_G(const double *KtT, const double *L, const double *u, int M, int N, double *y,
+                         cudaStream_t s);
 // CTAs of the persistent kernel that fit one SM at this shape (shared memory included).
 int sweep_ctas_per_sm_f32(const LaunchShape &shape, int kv, bool batch);
 int sweep_ctas_per_sm_f64(const LaunchShape &shape, int kv, bool batch);
@@ -158,6 +187,8 @@ constexpr int kBinLevels = 8;
 // has at most 8 warps, two per SM sub-partition, and a thread may hold up to
 // 255 registers (9 warps would put three on one sub-partition: 168).
 constexpr int kMaxConsumers = 7;
+// Deepest ring of move records (stages) a launch may use.
+constexpr int kMaxRingDepth = 48;
 constexpr int kMaxKvF32 = 16;   // 64 floats per lane
 constexpr int kMaxKvF64 = 32;   // 64 doubles per lane
 

@@ -227,12 +227,6 @@ __global__ void colsum_kernel(const T *F, int ldF, int chains, int N, double *Sf
     Sf[n] += a;
 }
 
-__global__ void add_f32_to_f64(const float *x, double *y, long long n)
-{
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] += (double)x[i];
-}
-
 // shift[n] = mean over chains of f[q][n] (the centre of all later snapshots)
 template <class T>
 __global__ void shift_kernel(const T *F, int ldF, int chains, int N, double *shift)
@@ -263,22 +257,6 @@ __global__ void kshift_kernel(const double *Kth, const double *shift, int M, int
     double a = 0.0;
     for (int n = 0; n < N; ++n) a += Kth[((size_t)pi * M + m) * N + n] * shift[n];
     kshift[i] = a;
-}
-
-// Scores of parameter p: s[q] = r~_q . (Y[:, q] + kshift_p) with Y = K~_theta_p D^T
-// (M x chains, column-major) of the centred snapshot; one warp per chain, FP64.
-template <class T>
-__global__ void score_kernel(const T *R, int ldR, const T *Y, const double *kshift, int M, int chains, int P,
-                             int pi, double *Sq)
-{
-    const long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (q >= chains) return;
-    double a = 0.0;
-    for (int m = lane; m < M; m += 32)
-        a += (double)R[(size_t)q * ldR + m] * ((double)Y[(size_t)q * M + m] + kshift[(size_t)pi * M + m]);
-    for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
-    if (lane == 0) Sq[(size_t)q * P + pi] = a;
 }
 
 // Sfs[n*P + p] += sum_q f[q][n] s[q][p]; Ss[p] += sum_q s[q][p] (thread n < P also does Ss).
@@ -338,9 +316,10 @@ int round_up_int(int x, int a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
     size_t counters, F, R, S1, S2, chi2;
-    size_t Sff, Sf, Sfs, Ss, Gtmp, Y, Sq;   // snapshot moments for the backward pass
+    size_t Sff, Sf, Sfs, Ss, Y, Sq;         // snapshot moments for the backward pass
     size_t shift, kshift, D;                // centring of the snapshots
     size_t S1p, bpend, bacc1, bacc2, bcount; // binning of the Monte Carlo error
+    size_t fref, rref;                       // reference state of the tensor-core refresh
     size_t total;
     int ldF, ldR;
 };
@@ -350,7 +329,7 @@ struct WsLayout {
 // device buffers of one precision
 struct PrecBuffers {
     void *V = nullptr, *R = nullptr, *d = nullptr, *invd = nullptr, *meta = nullptr,
-         *rec = nullptr, *Ut = nullptr, *Um = nullptr;
+         *rec = nullptr, *Ut = nullptr, *Um = nullptr, *Us = nullptr;
     void *prior_am1 = nullptr;   // a_n - 1 of the gamma prior (nullptr: flat)
 };
 
@@ -361,7 +340,7 @@ struct asm_problem {
     std::vector<double> w;
     double f0 = 0.0;
     int max_nb = 0, max_np = 0;
-    long long totV = 0, totR = 0, totd = 0, totU = 0, totRec = 0;
+    long long totV = 0, totR = 0, totd = 0, totU = 0, totRec = 0, totUs = 0;
     int max_rec = 0;   // largest record (elements)
     // device
     int *d_level_first = nullptr, *d_level_nblocks = nullptr;
@@ -376,7 +355,6 @@ struct asm_problem {
     float *d_Kth32 = nullptr;
     double *d_w = nullptr, *d_dw = nullptr;   // weights and dw/dtheta (P x N)
     double *d_vjp = nullptr;               // scratch of asm_backward: v', v, u (N each), y (M), g (P)
-    cublasHandle_t blas = nullptr;
     bool moments = false;
     long long nsnap = 0;                   // chain snapshots in the moments
     PrecBuffers b64, b32;
@@ -402,14 +380,16 @@ struct asm_problem {
     cudaGraphExec_t gexec = nullptr;
     struct GraphKey {
         const void *ws_all = nullptr;
-        int chains = 0, precision = -1, kv = 0, ctas = 0, S = 0, consumers = 0, depth = 0, n_items = 0, minb = 0;
+        int chains = 0, precision = -1, kv = 0, ctas = 0, S = 0, consumers = 0, depth = 0, n_items = 0, minb = 0,
+            ubytes = 0;
         size_t refresh_smem = 0;
         unsigned long long seed = 0, problem_id = 0, chain_offset = 0;
         bool operator==(const GraphKey &o) const
         {
             return ws_all == o.ws_all && chains == o.chains && precision == o.precision && kv == o.kv &&
                    ctas == o.ctas && S == o.S && consumers == o.consumers && depth == o.depth &&
-                   n_items == o.n_items && minb == o.minb && refresh_smem == o.refresh_smem && seed == o.seed &&
+                   n_items == o.n_items && minb == o.minb && ubytes == o.ubytes && refresh_smem == o.refresh_smem &&
+                   seed == o.seed &&
                    problem_id == o.problem_id && chain_offset == o.chain_offset;
         }
     } gkey;
@@ -446,8 +426,7 @@ WsLayout ws_layout(const asm_problem *p, int chains, int precision)
     L.Sf = off; off = align_up(off + N * 8, 256);
     L.Sfs = off; off = align_up(off + N * std::max<size_t>(P, 1) * 8, 256);
     L.Ss = off; off = align_up(off + std::max<size_t>(P, 1) * 8, 256);
-    L.Gtmp = off; off = align_up(off + (precision == ASM_FP64 ? 0 : N * N * 4), 256);
-    L.Y = off; off = align_up(off + (P ? (size_t)chains * p->M * es : 0), 256);
+    L.Y = off; off = align_up(off + (P ? (size_t)chains * P * p->M * es : 0), 256);
     L.Sq = off; off = align_up(off + (size_t)chains * std::max<size_t>(P, 1) * 8, 256);
     L.shift = off; off = align_up(off + N * 8, 256);
     L.kshift = off; off = align_up(off + (size_t)p->M * std::max<size_t>(P, 1) * 8, 256);
@@ -458,6 +437,8 @@ WsLayout ws_layout(const asm_problem *p, int chains, int precision)
     L.bacc1 = off; off = align_up(off + binned, 256);
     L.bacc2 = off; off = align_up(off + binned, 256);
     L.bcount = off; off = align_up(off + (size_t)chains * 4, 256);
+    L.fref = off; off = align_up(off + N * 4, 256);
+    L.rref = off; off = align_up(off + (size_t)p->M * 8, 256);
     L.total = off;
     return L;
 }
@@ -512,7 +493,7 @@ int upload(void **dst, const std::vector<T> &src)
 
 void free_prec(PrecBuffers &b)
 {
-    void *ptrs[] = {b.V, b.R, b.d, b.invd, b.meta, b.rec, b.Ut, b.Um, b.prior_am1};
+    void *ptrs[] = {b.V, b.R, b.d, b.invd, b.meta, b.rec, b.Ut, b.Um, b.Us, b.prior_am1};
     for (void *x : ptrs)
         if (x) cudaFree(x);
     b = PrecBuffers{};
@@ -525,7 +506,44 @@ struct HostFactors {
     std::vector<std::vector<double>> d;    // per block, n
     std::vector<std::vector<double>> V;    // per block, n x n mode-major
     std::vector<std::vector<double>> U;    // per block, np x M mode-major
+    std::vector<std::vector<double>> dres; // per block, n: |K~_b V_j| for the residual update
 };
+
+// The residual moves by K~_b V_j delta whatever the draw of mode j was.  For a
+// mode sampled flat (d = 0: numerically zero, or below the threshold of reading
+// R2 with a sign-changing V_j) its small K~_b V_j is formed here in FP64, and U_j
+// and dres_j are set to its direction and length, so that the exit update
+// r~ -= U_b (dres delta) keeps the tracked residual equal to g~ - K~ f (the
+// conditional means of weak modes are sensitive to a residual that misses it).
+// Modes j >= np lie in the exact null space of the block: nothing to add.
+void complete_residual_update(const asm_problem *p, HostFactors &hf)
+{
+    const int M = p->M, N = p->N;
+    hf.dres.resize(p->blocks.size());
+    for (size_t b = 0; b < p->blocks.size(); ++b) {
+        const BlockDesc &B = p->blocks[b];
+        std::vector<double> &dr = hf.dres[b];
+        dr.assign(B.n, 0.0);
+        for (int j = 0; j < B.np; ++j) {
+            if (hf.d[b][j] > 0.0) {
+                dr[j] = hf.d[b][j];
+                continue;
+            }
+            const double *v = &hf.V[b][(size_t)j * B.n];
+            std::vector<double> w(M, 0.0);
+            double nrm2 = 0.0;
+            for (int m = 0; m < M; ++m) {
+                double a = 0.0;
+                for (int i = 0; i < B.n; ++i) a += hf.Kt[(size_t)m * N + B.start + i] * v[i];
+                w[m] = a;
+                nrm2 += a * a;
+            }
+            const double nrm = std::sqrt(nrm2);
+            dr[j] = nrm;
+            for (int m = 0; m < M; ++m) hf.U[b][(size_t)j * M + m] = nrm > 0.0 ? w[m] / nrm : 0.0;
+        }
+    }
+}
 
 #define CK_CUDA(x) do { if ((x) != cudaSuccess) { rc = ASM_ERR_CUDA; goto done; } } while (0)
 #define CK_CUBLAS(x) do { if ((x) != CUBLAS_STATUS_SUCCESS) { rc = ASM_ERR_CUDA; goto done; } } while (0)
@@ -706,11 +724,13 @@ int whiten_dK(asm_problem *p, const double *dK)
     int rc = ASM_OK;
     const double one = 1.0;
     std::vector<float> h32;
+    cublasHandle_t bh = nullptr;   // set-up only: the sampling and backward paths use no library
+    CK_CUBLAS(cublasCreate(&bh));
     CK_CUDA(cudaMalloc(&p->d_Kth64, sizeof(double) * (size_t)P * M * N));
     CK_CUDA(cudaMalloc(&p->d_Kth32, sizeof(float) * (size_t)P * M * N));
     CK_CUDA(cudaMemcpy(p->d_Kth64, dK, sizeof(double) * (size_t)P * M * N, cudaMemcpyHostToDevice));
     for (int pi = 0; pi < P; ++pi)
-        CK_CUBLAS(cublasDtrsm(p->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T,
+        CK_CUBLAS(cublasDtrsm(bh, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T,
                               CUBLAS_DIAG_NON_UNIT, N, M, &one, p->d_L, M, p->d_Kth64 + (size_t)pi * M * N, N));
     {
         std::vector<double> h((size_t)P * M * N);
@@ -719,6 +739,7 @@ int whiten_dK(asm_problem *p, const double *dK)
     }
     CK_CUDA(cudaMemcpy(p->d_Kth32, h32.data(), sizeof(float) * h32.size(), cudaMemcpyHostToDevice));
 done:
+    if (bh) cublasDestroy(bh);
     return rc;
 }
 
@@ -732,7 +753,8 @@ int build_precision(asm_problem *p, const HostFactors &hf, PrecBuffers &out)
     std::vector<T> V(p->totV, T(0)), R(p->totR, nan), d(p->totd, T(0)),
         invd(p->totd, T(0)), meta((size_t)p->totd * MW, T(0)), rec(std::max<long long>(p->totRec, 1), T(0)),
         Ut(std::max<long long>(p->totU, 1), T(0)),
-        Um(std::max<long long>(p->totU, 1), T(0));
+        Um(std::max<long long>(p->totU, 1), T(0)),
+        Us(p->totUs + 4, T(0));   // + 4: a copy rounded up to 16 bytes stays inside
     for (int b = 0; b < p->n_blocks; ++b) {
         const BlockDesc &B = p->blocks[b];
         const std::vector<double> &hd = hf.d[b], &hV = hf.V[b], &hU = hf.U[b];
@@ -754,8 +776,9 @@ int build_precision(asm_problem *p, const HostFactors &hf, PrecBuffers &out)
             for (int m = 0; m < M; ++m) {
                 Ut[B.offU + (size_t)j * M + m] = (T)hU[(size_t)j * M + m];
                 Um[B.offU + (size_t)m * B.np + j] = (T)hU[(size_t)j * M + m];
+                Us[B.offUs + (size_t)j * B.usr + m] = (T)hU[(size_t)j * M + m];
             }
-        // move records: {V_j, R_{j+1}, d_j, 1/d_j}
+        // move records: {V_j, R_{j+1}, d_j, 1/d_j, dres_j}
         for (int j = 0; j < B.n; ++j) {
             T *r = &rec[B.offRec + (size_t)j * B.recstride];
             for (int i = 0; i < B.rs; ++i) {
@@ -764,13 +787,14 @@ int build_precision(asm_problem *p, const HostFactors &hf, PrecBuffers &out)
             }
             r[2 * B.rs] = d[B.offd + j];
             r[2 * B.rs + 1] = invd[B.offd + j];
+            r[2 * B.rs + 2] = (T)hf.dres[b][j];
         }
     }
     int rc;
     if ((rc = upload(&out.V, V)) || (rc = upload(&out.R, R)) ||
         (rc = upload(&out.d, d)) || (rc = upload(&out.invd, invd)) || (rc = upload(&out.meta, meta)) || (rc = upload(&out.rec, rec)) ||
         (rc = upload(&out.Ut, Ut)) ||
-        (rc = upload(&out.Um, Um)))
+        (rc = upload(&out.Um, Um)) || (rc = upload(&out.Us, Us)))
         return rc;
     return ASM_OK;
 }
@@ -827,6 +851,7 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.pd.invd = (const T *)b.invd;
     sp.pd.Ut = (const T *)b.Ut;
     sp.pd.Um = (const T *)b.Um;
+    sp.pd.Us = (const T *)b.Us;
     char *ws = (char *)p->ws;
     sp.F = (T *)(ws + L.F);
     sp.ldF = L.ldF;
@@ -854,6 +879,8 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.bacc2 = (double *)(ws + L.bacc2);
     sp.bcount = (int *)(ws + L.bcount);
     sp.f0 = p->f0;
+    sp.fref = (float *)(ws + L.fref);
+    sp.rref = (double *)(ws + L.rref);
     return sp;
 }
 
@@ -876,13 +903,14 @@ int ctas_per_sm(int precision, const LaunchShape &sh, int kv, bool batch)
 
 template <class T>
 bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long long total_warps, int kv,
-                bool batch, int want_consumers, int minb, bool prior)
+                bool batch, int want_consumers, int minb, bool prior, const std::vector<int> &ublk_bytes)
 {
     sh.minb = prior ? 1 : minb;   // the prior's kernels exist for one CTA per SM
     sh.prior = prior ? 1 : 0;
     sh.wait_limit = kWaitLimit;
     sh.stall = 0;
     constexpr int kSMs = 152;
+    constexpr int kMinRing = 8;   // the U stages may not squeeze the record ring below this depth
     const int TW = 32 / S;
     const int prec = sizeof(T) == 8 ? ASM_FP64 : ASM_MIXED;
     sh.S = S;
@@ -897,32 +925,51 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
         if (c >= 1 && c <= kMaxConsumers) consumers = c;
     }
     sh.stage_bytes = (int)align_up((size_t)max_rec * sizeof(T), 128);
+    // per-team state, then the ring's barriers (full, empty: 8 bytes per stage each), the
+    // U stages' barriers (4 x 8 bytes, padded to 128) and the U stages
+    constexpr int kBarBytes = 8 * kMaxRingDepth;
     auto fixed = [&](int c) {
-        return align_up((size_t)c * TW * (2 * sh.cpad + sh.mpad + 8 * S) * sizeof(T), 128) + 256;
+        return align_up((size_t)c * TW * (2 * sh.cpad + sh.mpad + 8 * S) * sizeof(T), 128) + 2 * kBarBytes + 128;
     };
-    int max_depth = 16;
+    int max_depth = kMaxRingDepth;
     if (const char *e = std::getenv("ASM_RING_DEPTH")) {            // tuning override
         const int d = std::atoi(e);
-        if (d >= 2 && d <= 16) max_depth = d;
+        if (d >= 2 && d <= kMaxRingDepth) max_depth = d;
     }
+    bool stage_u = std::getenv("ASM_NO_U_STAGE") == nullptr;       // tuning override
     for (; consumers >= 1; --consumers) {
         LaunchShape probe = sh;   // no dynamic shared memory: the register limit alone
         probe.consumers = consumers;
         probe.depth = 0;
         probe.off_stages = 0;
+        probe.ubytes = 0;
         const int by_regs = std::max(1, ctas_per_sm(prec, probe, kv, batch));
         const long long ctas = (total_warps + consumers - 1) / consumers;
         const int per_sm = (int)std::min<long long>(by_regs, std::max<long long>(1, (ctas + kSMs - 1) / kSMs));
         const size_t budget = std::min<size_t>(220 * 1024 / per_sm, 227 * 1024);
+        // U stages: as large as the largest block U that leaves room for a ring of kMinRing
+        size_t ub = 0;
+        if (stage_u) {
+            const size_t room = budget > fixed(consumers) + (size_t)kMinRing * sh.stage_bytes
+                                    ? (budget - fixed(consumers) - (size_t)kMinRing * sh.stage_bytes) / 2
+                                    : 0;
+            for (int b : ublk_bytes) {
+                const size_t bb = align_up((size_t)b, 128);
+                if (bb <= room && bb > ub) ub = bb;
+            }
+        }
         int depth = max_depth;
-        while (depth > 2 && fixed(consumers) + (size_t)depth * sh.stage_bytes > budget) --depth;
-        if (fixed(consumers) + (size_t)depth * sh.stage_bytes <= budget || consumers == 1) {
-            if (fixed(consumers) + (size_t)depth * sh.stage_bytes > 227 * 1024) return false;
+        while (depth > 2 && fixed(consumers) + 2 * ub + (size_t)depth * sh.stage_bytes > budget) --depth;
+        if (fixed(consumers) + 2 * ub + (size_t)depth * sh.stage_bytes <= budget || consumers == 1) {
+            if (fixed(consumers) + 2 * ub + (size_t)depth * sh.stage_bytes > 227 * 1024) return false;
             sh.consumers = consumers;
             sh.depth = depth;
+            sh.ubytes = (int)ub;
             sh.off_full = (int)align_up((size_t)consumers * TW * (2 * sh.cpad + sh.mpad + 8 * S) * sizeof(T), 128);
-            sh.off_empty = sh.off_full + 128;
-            sh.off_stages = sh.off_full + 256;
+            sh.off_empty = sh.off_full + kBarBytes;
+            sh.off_ubar = sh.off_full + 2 * kBarBytes;
+            sh.off_ubuf = sh.off_ubar + 128;
+            sh.off_stages = sh.off_ubuf + 2 * (int)ub;
             return true;
         }
     }
@@ -963,41 +1010,20 @@ int moment_update(asm_problem *p, const WsLayout &L, int chains)
         ++p->other_launches;
     }
     const T *F = (const T *)(ws + L.D);
-    if (cublasSetStream(p->blas, p->stream) != CUBLAS_STATUS_SUCCESS) return ASM_ERR_CUDA;
-    if constexpr (sizeof(T) == 8) {
-        const double one = 1.0;
-        if (cublasDgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_T, N, N, chains, &one, F, L.ldF, F, L.ldF, &one,
-                        (double *)(ws + L.Sff), N) != CUBLAS_STATUS_SUCCESS)
-            return ASM_ERR_CUDA;
-    } else {
-        const float one = 1.f, zero = 0.f;
-        if (cublasSgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_T, N, N, chains, &one, F, L.ldF, F, L.ldF, &zero,
-                        (float *)(ws + L.Gtmp), N) != CUBLAS_STATUS_SUCCESS)
-            return ASM_ERR_CUDA;
-        const long long nn = (long long)N * N;
-        add_f32_to_f64<<<(unsigned)((nn + 255) / 256), 256, 0, p->stream>>>((const float *)(ws + L.Gtmp),
-                                                                            (double *)(ws + L.Sff), nn);
-        ++p->other_launches;
-    }
+    // Sff += D^T D (FP32 partial sums over slices of chains in the mixed path, added in FP64)
+    if (launch_gram(F, L.ldF, chains, N, (double *)(ws + L.Sff), p->stream) != cudaSuccess) return ASM_ERR_CUDA;
     colsum_kernel<T><<<(N + 127) / 128, 128, 0, p->stream>>>(F, L.ldF, chains, N, (double *)(ws + L.Sf));
-    ++p->other_launches;
-    for (int pi = 0; pi < p->P; ++pi) {
+    p->other_launches += 2;
+    if (p->P > 0) {
+        // Y = D K~_theta^T for every parameter at once, then the scores
         T *Y = (T *)(ws + L.Y);
-        cublasStatus_t st;
-        if constexpr (sizeof(T) == 8) {
-            const double one = 1.0, zero = 0.0;
-            st = cublasDgemm(p->blas, CUBLAS_OP_T, CUBLAS_OP_N, M, chains, N, &one, p->d_Kth64 + (size_t)pi * M * N,
-                             N, F, L.ldF, &zero, Y, M);
-        } else {
-            const float one = 1.f, zero = 0.f;
-            st = cublasSgemm(p->blas, CUBLAS_OP_T, CUBLAS_OP_N, M, chains, N, &one, p->d_Kth32 + (size_t)pi * M * N,
-                             N, F, L.ldF, &zero, Y, M);
-        }
-        if (st != CUBLAS_STATUS_SUCCESS) return ASM_ERR_CUDA;
-        score_kernel<T><<<(unsigned)(((long long)chains * 32 + 255) / 256), 256, 0, p->stream>>>(
-            (const T *)(ws + L.R), L.ldR, Y, (const double *)(ws + L.kshift), M, chains, p->P, pi,
-            (double *)(ws + L.Sq));
-        ++p->other_launches;
+        const T *Kth;
+        if constexpr (sizeof(T) == 8) Kth = p->d_Kth64; else Kth = p->d_Kth32;
+        if (launch_kth_product(F, L.ldF, chains, N, Kth, p->P * M, Y, p->stream) != cudaSuccess ||
+            launch_scores((const T *)(ws + L.R), L.ldR, (const T *)Y, (const double *)(ws + L.kshift), M, chains,
+                          p->P, (double *)(ws + L.Sq), p->stream) != cudaSuccess)
+            return ASM_ERR_CUDA;
+        p->other_launches += 2;
     }
     if (p->P > 0) {
         fs_kernel<T><<<(N + 127) / 128, 128, 0, p->stream>>>(F, L.ldF, (const double *)(ws + L.Sq), chains, N, p->P,
@@ -1050,6 +1076,11 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
         max_nb = std::max(max_nb, u->max_nb);
         max_N = std::max(max_N, u->N);
     }
+    // bytes of every block's U in its staging layout (np rows of usr elements, 16-byte multiple)
+    std::vector<int> ublk;
+    for (asm_problem *u : us)
+        for (const BlockDesc &B : u->blocks)
+            ublk.push_back((int)(((size_t)B.np * B.usr * sizeof(T) + 15) / 16 * 16));
     const int S = h->team;
     const int vec = 16 / (int)sizeof(T);
     const int kv = pick_kv(max_nb, vec, S, sizeof(T) == 8 ? kMaxKvF64 : kMaxKvF32);
@@ -1067,7 +1098,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
     bool prior = false;   // any problem with a gamma prior: the kernels with the acceptance step
     for (asm_problem *u : us) prior = prior || (sizeof(T) == 8 ? u->b64.prior_am1 : u->b32.prior_am1) != nullptr;
     LaunchShape sh{};
-    if (!plan_shape<T>(sh, S, max_rec, max_np, max_M, total_warps, kv, batch, h->tuned_consumers, minb, prior))
+    if (!plan_shape<T>(sh, S, max_rec, max_np, max_M, total_warps, kv, batch, h->tuned_consumers, minb, prior, ublk))
         return ASM_ERR_TOO_LARGE;
     bool stall = h->test_stall;
     for (asm_problem *u : us) stall = stall || u->test_stall;
@@ -1128,7 +1159,8 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
     auto refresh = [&](cudaStream_t st) {
         if constexpr (sizeof(T) == 4) {
             if (tc) {
-                return launch_refresh_tc(d_probs, (int)us.size(), chains, max_bn, true, st);
+                const cudaError_t e = launch_refresh_ref(d_probs, (int)us.size(), chains, st);
+                return e != cudaSuccess ? e : launch_refresh_tc(d_probs, (int)us.size(), chains, max_bn, true, st);
             }
         }
         refresh_all_kernel<T><<<n_refresh, 128, rsmem, st>>>(d_probs, chains, 1);
@@ -1155,6 +1187,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             key.depth = sh.depth;
             key.n_items = sh.n_items;
             key.minb = sh.minb + 4 * sh.prior + 8 * sh.stall;
+            key.ubytes = sh.ubytes;
             key.refresh_smem = tc ? refresh_tc_smem(max_bn) + 1 : rsmem;
             key.seed = p0.seed;   // by value in a single problem's launch
             key.problem_id = p0.problem_id;
@@ -1239,7 +1272,7 @@ int init_chains(asm_problem *p, const WsLayout &L, int chains)
     if (cudaMemsetAsync(ws + L.R, 0, (size_t)chains * L.ldR * sizeof(T), p->stream) != cudaSuccess)
         return ASM_ERR_CUDA;
     // snapshot moments of the backward pass start at zero
-    if (cudaMemsetAsync(ws + L.Sff, 0, L.Gtmp - L.Sff, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
+    if (cudaMemsetAsync(ws + L.Sff, 0, L.Y - L.Sff, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
     // binning state starts empty
     if (cudaMemsetAsync(ws + L.S1p, 0, L.bcount + (size_t)chains * 4 - L.S1p, p->stream) != cudaSuccess)
         return ASM_ERR_CUDA;
@@ -1331,7 +1364,7 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
         nb += ds->level_nblocks[l];
     }
     p->n_blocks = nb;
-    long long oV = 0, oR = 0, od = 0, oU = 0, oRec = 0;
+    long long oV = 0, oR = 0, od = 0, oU = 0, oRec = 0, oUs = 0;
     for (int l = 0; l < ds->n_levels; ++l) {
         const int *st = ds->block_start + p->level_first[l];
         for (int b = 0; b < ds->level_nblocks[l]; ++b) {
@@ -1346,6 +1379,8 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
             B.offR = oR; oR += (long long)(B.n + 1) * B.rs;
             B.offd = od; od += B.n;
             B.offU = oU; oU += (long long)B.np * M;
+            B.usr = M | 1;
+            B.offUs = oUs; oUs += ((long long)B.np * B.usr + 3) / 4 * 4;   // 16-byte aligned in both precisions
             B.recstride = 2 * B.rs + 16;   // elements; 16 holds the mode data in both precisions
             B.offRec = oRec; oRec += (long long)B.n * B.recstride;
             p->max_rec = std::max(p->max_rec, B.recstride);
@@ -1354,7 +1389,7 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
             p->max_np = std::max(p->max_np, B.np);
         }
     }
-    p->totV = oV; p->totR = oR; p->totd = od; p->totU = oU; p->totRec = oRec;
+    p->totV = oV; p->totR = oR; p->totd = od; p->totU = oU; p->totRec = oRec; p->totUs = oUs;
     p->w.assign(N, 1.0);
     if (ds->w) {
         if (!all_finite(ds->w, N)) { asm_destroy(p); return ASM_ERR_NONFINITE; }
@@ -1406,12 +1441,12 @@ int asm_setup(const asm_desc *ds, asm_problem **out)
         rc = device_factorize(ds, p, hf, &p->d_L);
         if (rc != ASM_OK) { asm_destroy(p); return rc; }
     }
+    complete_residual_update(p, hf);
     if (given && ds->C) {
         if (!all_finite(ds->C, (size_t)M * M)) { asm_destroy(p); return ASM_ERR_NONFINITE; }
         rc = device_cholesky(ds->C, M, &p->d_L);
         if (rc != ASM_OK) { asm_destroy(p); return rc; }
     }
-    if (cublasCreate(&p->blas) != CUBLAS_STATUS_SUCCESS) { asm_destroy(p); return ASM_ERR_CUDA; }
     if (p->P > 0) {
         if (!p->d_L) { asm_destroy(p); return ASM_ERR_ARG; }   // theta-gradients need C
         rc = whiten_dK(p, ds->dK_dtheta);
@@ -1883,12 +1918,8 @@ int asm_backward(asm_problem *p, const double *v, double *grad_G, double *grad_t
     if (grad_G) {
         vjp_cov_kernel<<<(N + 127) / 128, 128, 0, p->stream>>>((const double *)(ws + L.Sff),
                                                                (const double *)(ws + L.Sf), ns, d_vp, N, d_u);
-        const double one = 1.0, zero = 0.0;
-        if (cudaGetLastError() != cudaSuccess || cublasSetStream(p->blas, p->stream) != CUBLAS_STATUS_SUCCESS ||
-            cublasDgemv(p->blas, CUBLAS_OP_N, M, N, &one, p->d_KtT, M, d_u, 1, &zero, d_y, 1) !=
-                CUBLAS_STATUS_SUCCESS ||
-            cublasDtrsv(p->blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, M, p->d_L, M, d_y, 1) !=
-                CUBLAS_STATUS_SUCCESS ||
+        // C^{-1} K u = L^{-T} (K~ u): hand-written product and triangular solve
+        if (cudaGetLastError() != cudaSuccess || launch_vjp_G(p->d_KtT, p->d_L, d_u, M, N, d_y, p->stream) != cudaSuccess ||
             cudaMemcpyAsync(grad_G, d_y, sizeof(double) * M, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
             return ASM_ERR_CUDA;
     }
@@ -2030,7 +2061,7 @@ struct CheckpointHeader {
     int64_t sweeps_done, kept, ws_bytes;
     int64_t kept_since;   // first sweep of the unbroken kept run (binning of a continuation)
 };
-constexpr uint64_t kCheckpointVersion = 2;
+constexpr uint64_t kCheckpointVersion = 3;
 constexpr uint64_t kCheckpointMagic = 0x41534d434b505431ull;   // "ASMCKPT1"
 }  // namespace
 
@@ -2119,7 +2150,6 @@ void asm_destroy(asm_problem *p)
     p->kids.clear();
     void *ptrs[] = {p->d_level_first, p->d_level_nblocks, p->d_blocks, p->d_KtT, p->d_gt, p->d_Khi, p->d_Klo, p->d_L,
                     p->d_Kth64, p->d_Kth32, p->d_w, p->d_dw, p->d_vjp};
-    if (p->blas) cublasDestroy(p->blas);
     for (void *x : ptrs)
         if (x) cudaFree(x);
     free_prec(p->b64);

@@ -1,15 +1,25 @@
 // Residual refresh of the mixed-precision path on the 5th-generation tensor
 // cores: R~ = 1 g~^T - F K~^T for all chains of every problem of a launch, the
-// product in split precision (3xTF32: F_hi K_hi + F_hi K_lo + F_lo K_hi, FP32
+// product in split precision (3xTF32: A_hi K_hi + A_hi K_lo + A_lo K_hi, FP32
 // accumulation in tensor memory), the difference from g~, chi^2 = |r~|^2 and the
 // resync drift in FP64.
+//
+// Centring.  g~ and K~ f are large against their difference r~ when the data
+// are accurate (|g~| ~ 1e2 .. 1e5 against |r~| ~ sqrt(M)), so an FP32
+// accumulation of K~ f would leave an error of 2^-24 |g~| in r~.  The product
+// is therefore taken of the centred states A = f - fref, with fref the mean
+// chain state of the problem at this refresh, and r~ = r_ref - K~ A with
+// r_ref = g~ - K~ fref formed in FP64 once per refresh: K~ A is of the size of
+// the posterior spread, and its FP32 accumulation error shrinks with it.  The
+// difference f - fref is formed exactly in FP64 before the split into TF32
+// high and FP32 low parts.
 //
 // One CTA of 128 threads owns 128 chains of one problem (the MMA's M = 128
 // rows, one TMEM lane per chain) and loops over the problem's M_tau tiles
 // (N of the MMA, <= 256 columns of FP32 accumulator) and over k-tiles of 32
 // grid points.  Each k-tile is staged by all threads into shared memory in
 // the canonical K-major layout without swizzle (core matrices of 8 rows x 16
-// bytes), F split into TF32 high and low parts on the way; K~ comes split
+// bytes), A split into TF32 high and low parts on the way; K~ comes split
 // from set-up.  Two stages alternate: thread 0 issues the 12 tcgen05.mma of a
 // stage and commits them to the stage's mbarrier, which the threads wait on
 // before staging into it again.  Waits are bounded (timeouts are counted).
@@ -112,6 +122,59 @@ __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int ld
     }
 }
 
+// The same layout for the centred chain states: rows of f - fref, the
+// difference exact in FP64, split into a TF32 high part and an FP32 remainder.
+__device__ __forceinline__ void stage_centred(const float *__restrict__ F, int ld, const float *__restrict__ fref,
+                                              int rows_valid, int cols_valid, int row0, int k0, unsigned char *hi,
+                                              unsigned char *lo)
+{
+    const int n4 = kTcRows * (kTcBK / 4);
+    for (int e = threadIdx.x; e < n4; e += kTcThreads) {
+        const int r8 = e & 7, kc = (e >> 3) & 7, rg = e >> 6;
+        const int row = row0 + rg * 8 + r8;
+        const int col = k0 + kc * 4;
+        float x[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+        if (row < rows_valid && col < cols_valid) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(F + (size_t)row * ld + col));
+            x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (col + j < cols_valid) c[j] = fref[col + j];
+                else x[j] = 0.f;
+            }
+        }
+        float h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const double d = (double)x[j] - (double)c[j];
+            h[j] = tf32_round((float)d);
+            l[j] = (float)(d - (double)h[j]);
+        }
+        const int off = (rg * 8 + kc) * 128 + r8 * 16;
+        *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+// Reference state of one problem per CTA: fref = mean of the chain states
+// (FP32, summed in chain order) and r_ref = g~ - K~ fref in FP64.
+__global__ void refresh_ref_kernel(const SweepParams<float> *__restrict__ probs, int chains)
+{
+    const SweepParams<float> &p = probs[blockIdx.x];
+    const float inv = 1.0f / (float)chains;
+    for (int n = threadIdx.x; n < p.N; n += blockDim.x) {
+        float a = 0.f;
+        for (int q = 0; q < chains; ++q) a += p.F[(size_t)q * p.ldF + n];
+        p.fref[n] = a * inv;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < p.M; m += blockDim.x) {
+        double a = p.gt[m];
+        for (int n = 0; n < p.N; ++n) a -= p.KtT[(size_t)n * p.M + m] * (double)p.fref[n];
+        p.rref[m] = a;
+    }
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1)
 refresh_tc_kernel(const SweepParams<float> *__restrict__ probs, int chains, int stage_bytes, int track_drift)
 {
@@ -163,7 +226,7 @@ refresh_tc_kernel(const SweepParams<float> *__restrict__ probs, int chains, int 
                 fail = 1;
                 break;
             }
-            stage_rows(p.F, p.ldF, chains, N, row0, kt * kTcBK, kTcRows, a_hi, a_lo);
+            stage_centred(p.F, p.ldF, p.fref, chains, N, row0, kt * kTcBK, a_hi, a_lo);
             stage_rows(p.Khi, p.ldK, M, N, m0, kt * kTcBK, BN, b_hi, nullptr);
             stage_rows(p.Klo, p.ldK, M, N, m0, kt * kTcBK, BN, b_lo, nullptr);
             fence_proxy_async_smem();   // generic-proxy writes become visible to the tensor cores
@@ -204,7 +267,7 @@ refresh_tc_kernel(const SweepParams<float> *__restrict__ probs, int chains, int 
                 for (int j = 0; j < 16; ++j) {
                     const int m = m0 + c0 + j;
                     if (m < M) {
-                        const double r = p.gt[m] - (double)v[j];
+                        const double r = p.rref[m] - (double)v[j];
                         const double old = (double)Rq[m];
                         sum_old += old * old;
                         sum_new += r * r;
@@ -275,6 +338,12 @@ cudaError_t launch_refresh_tc(const SweepParams<float> *probs, int n_problems, i
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((chains + kTcRows - 1) / kTcRows), (unsigned)n_problems);
     refresh_tc_kernel<<<grid, kTcThreads, smem, s>>>(probs, chains, stage_bytes, track_drift ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_ref(const SweepParams<float> *probs, int n_problems, int chains, cudaStream_t s)
+{
+    refresh_ref_kernel<<<(unsigned)n_problems, 256, 0, s>>>(probs, chains);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,8 @@
 //   delta     ~ N(c_j/d_j, 1/d_j^2) on [lo, hi] by the inverse CDF (flat if d_j = 0)
 //   pass      f += delta V_j, clamp at 0, and the bounds of mode j+1 in the same
 //             sweep over the registers
-//   w_j       = d_j delta  (the residual moves by -w_j U_j; c_j is not needed again)
+//   w_j       = dres_j delta  (the residual moves by -w_j U_j, dres_j = |K~_b V_j|;
+//               c_j is not needed again)
 // Block entry computes c = U_b^T r~, block exit applies r~ -= U_b w.
 #pragma once
 
@@ -104,22 +105,28 @@ template <> struct TailTraits<float> {
 };
 
 // x ~ N(0,1) restricted to [a, b], 0 <= a < b <= inf, by Q(x) = (1-u)Q(a) + uQ(b).
-// Returns the offset y = x - a.  For a >= 5 the equation is solved for y by
-// Newton's method on log Q (concave, so the iterates are monotone after the
-// first step), with Q(b)/Q(a) formed through erfcx to keep narrow intervals
-// accurate.
+// Returns the offset y = x - a.  The equation in y,
+//   log Q(a + y) - log Q(a) = dt,  dt = log((1-u) + u Q(b)/Q(a)),
+// is solved by Newton's method on log Q (concave, so the iterates are monotone
+// after the first step), with Q(b)/Q(a) formed through erfcx to keep narrow
+// intervals accurate.  The start is the exponential tail's inverse for a >= 5
+// and, below, y = -Phi^{-1}(q) - a with q = (1-u)Q(a) + uQ(b): accurate to a
+// few ulp of a, which FP32 keeps; in FP64 the offset form refines it so that y
+// keeps its relative accuracy however small it is.
 template <class T>
 __device__ __forceinline__ T right_tail(T a, T b, T u, int &capped)
 {
     const T kRsqrt2 = T(0.70710678118654752440);
     const T kSqrtPiOver2 = T(1.25331413731550025121);
+    constexpr bool kRefine = sizeof(T) == 8;
     T y;
     if (a < T(5)) {
         const T qa = m_phi(-a);
         const T qb = isinf(b) ? T(0) : m_phi(-b);
         const T q = (T(1) - u) * qa + u * qb;
         y = -m_phiinv(q) - a;
-    } else {
+    }
+    if (a >= T(5) || (kRefine && a > T(0))) {
         const T exa = m_erfcx(a * kRsqrt2);
         T r = T(0), em = T(-1);
         if (!isinf(b)) {
@@ -128,7 +135,7 @@ __device__ __forceinline__ T right_tail(T a, T b, T u, int &capped)
             em = m_expm1(lr);
         }
         const T dt = r < T(0.5) ? m_log((T(1) - u) + u * r) : m_log1p(u * em);
-        y = -dt / a;
+        if (a >= T(5)) y = -dt / a;
         int it = 0;
         for (; it < TailTraits<T>::nmax; ++it) {
             const T exy = m_erfcx((a + y) * kRsqrt2);
@@ -188,14 +195,22 @@ __device__ __forceinline__ T narrow_cdf(T a, T t)
 }
 
 // Narrow interval (w (|a| + w) <= 1/2, the Gaussian nearly flat across it):
-// solve I(t) = u I(w) by Newton's method from t = u w.  The offset t from the
-// lower end keeps its relative accuracy however narrow the interval is.
+// solve I(t) = u I(w) by Newton's method.  The start is the inverse CDF of the
+// exponential law whose rate is the log-density's slope at the interval's
+// midpoint, lam = a + w/2: the neglected curvature changes the log-density by
+// at most w^2/8 across the interval, so one or two steps converge where the
+// flat start t = u w needed four.  The offset t from the lower end keeps its
+// relative accuracy however narrow the interval is.
 template <class T>
 __device__ __forceinline__ T narrow_offset(T a, T w, T u, int &capped)
 {
     using GL = GaussLegendre<T>;
     const T target = u * narrow_cdf(a, w);
-    T t = u * w;
+    const T lam = a + T(0.5) * w;
+    const T x = lam * w;
+    T t = m_abs(x) < T(1e-3) ? u * w * (T(1) - T(0.5) * x * (T(1) - u))   // the series for small lam w
+                             : -m_log1p(u * m_expm1(-x)) / lam;
+    t = m_min(m_max(t, T(0)), w);
     int it = 0;
     for (; it < GL::nmax; ++it) {
         const T step = (narrow_cdf(a, t) - target) / m_exp(-t * (a + T(0.5) * t));
@@ -489,7 +504,20 @@ struct RingPos {
     unsigned g;             // records in this launch (< 2^32: one launch is at most 64 sweeps)
     int slot;
     unsigned phase;
+    unsigned ug;            // block visits whose U went through the two U stages
 };
+
+// Bytes of block B's U in its staging layout, and whether it goes through the U stages.
+template <class T>
+__device__ __forceinline__ unsigned u_stage_bytes(const BlockDesc &B)
+{
+    return (unsigned)((((size_t)B.np * B.usr * sizeof(T)) + 15) / 16 * 16);
+}
+template <class T>
+__device__ __forceinline__ bool u_staged(const LaunchShape &sh, const BlockDesc &B)
+{
+    return sh.ubytes > 0 && u_stage_bytes<T>(B) <= (unsigned)sh.ubytes;
+}
 
 __device__ __forceinline__ void ring_next(RingPos &r, int depth)
 {
@@ -559,7 +587,8 @@ __device__ __forceinline__ void mbar_arrive_lane0(unsigned long long *bar, int l
 template <class T>
 __device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchShape &sh, const SweepRange &rg,
                                         unsigned long long *full, unsigned long long *empty,
-                                        unsigned char *stages, RingPos &rp, bool &failed)
+                                        unsigned char *stages, unsigned long long *ufull, unsigned long long *uempty,
+                                        unsigned char *ubuf, RingPos &rp, bool &failed)
 {
     if ((threadIdx.x & 31) != 0 || rg.nsweeps <= 0 || failed || sh.stall) return;
     const int D = sh.depth;
@@ -568,8 +597,21 @@ __device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchSha
     c.s_end = rg.sweep0 + rg.nsweeps;
     c.done = false;
     cursor_start_sweep(c, p);
-    const unsigned g0 = rp.g;
+    const unsigned g0 = rp.g, ug0 = rp.ug;
     while (!c.done) {
+        // a block visit starts: its U into the next U stage (after that stage's previous
+        // U has been released by every consumer warp)
+        if (c.j == 0 && u_staged<T>(sh, c.B)) {
+            const unsigned us = rp.ug & 1u;
+            if (rp.ug >= 2u && !mbar_wait(uempty + us, ((rp.ug >> 1) & 1u) ^ 1u, sh.wait_limit)) {
+                failed = true;
+                break;
+            }
+            const unsigned ubytes = u_stage_bytes<T>(c.B);
+            mbar_expect_tx(ufull + us, ubytes);
+            bulk_g2s(ubuf + (size_t)us * sh.ubytes, p.pd.Us + c.B.offUs, ubytes, ufull + us);
+            ++rp.ug;
+        }
         // the slot's previous record (phase ^ 1) must have been released
         if (rp.g >= (unsigned)D && !mbar_wait(empty + rp.slot, rp.phase ^ 1u, sh.wait_limit)) {
             failed = true;
@@ -588,6 +630,8 @@ __device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchSha
         const unsigned from = g > g0 + (unsigned)D ? g - D : g0;
         for (unsigned k = from; k < g; ++k)
             mbar_wait(full + (k % (unsigned)D), (k / (unsigned)D) & 1u, sh.wait_limit);
+        const unsigned ufrom = rp.ug > ug0 + 2u ? rp.ug - 2u : ug0;
+        for (unsigned k = ufrom; k < rp.ug; ++k) mbar_wait(ufull + (k & 1u), (k >> 1) & 1u, sh.wait_limit);
         atomicAdd(&p.counters->timeouts, 1ull);
     }
 }
@@ -602,8 +646,8 @@ __device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchSha
 template <class T, int KV, bool PRIOR, bool WIDE>
 __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchShape &sh, const SweepRange &rg,
                                         int group, unsigned char *smem_raw, unsigned long long *full,
-                                        unsigned long long *empty, unsigned char *stages, RingPos &rp,
-                                        bool &failed)
+                                        unsigned long long *empty, unsigned char *stages, unsigned long long *ufull,
+                                        unsigned long long *uempty, unsigned char *ubuf, RingPos &rp, bool &failed)
 {
     constexpr int VEC = VecOf<T>::n;
     if (failed) return;
@@ -656,9 +700,40 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     const int nl = VEC * (k * S + sl) + v;
                     f[k][v] = (k < kcnt && nl < B.n) ? Fq[B.start + nl] : T(0);
                 }
+            // U of this block: from its U stage once the producer's copy has landed, else
+            // from global memory
+            const bool ust = u_staged<T>(sh, B);
+            const T *Us = nullptr;
+            if (ust) {
+                bool ok = mbar_test_wait(ufull + (rp.ug & 1u), (rp.ug >> 1) & 1u);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    ok = ok || mbar_wait(ufull + (rp.ug & 1u), (rp.ug >> 1) & 1u, sh.wait_limit);
+                    if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
+                        failed = true;
+                        break;
+                    }
+                }
+                Us = reinterpret_cast<const T *>(ubuf + (size_t)(rp.ug & 1u) * sh.ubytes);
+            }
             // c = U_b^T r~ (lanes split the modes; eight (WIDE: sixteen) loads in flight, eight
-            // partial sums, partial sum i taking the terms m = i mod 8 in increasing m)
+            // partial sums, partial sum i taking the terms m = i mod 8 in increasing m; the
+            // same sums in the same order from the U stage)
             const T *Um = p.pd.Um + B.offU;
+            if (ust) {
+                for (int j = sl; j < B.np; j += S) {
+                    const T *u = Us + (size_t)j * B.usr;
+                    T a[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) a[i] = T(0);
+                    int m = 0;
+                    for (; m + 7 < p.M; m += 8) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) a[i] = m_fma(u[m + i], rsm[m + i], a[i]);
+                    }
+                    for (; m < p.M; ++m) a[0] = m_fma(u[m], rsm[m], a[0]);
+                    csm[j] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+                }
+            } else
             for (int j = sl; j < B.np; j += S) {
                 T a[8];
 #pragma unroll
@@ -803,7 +878,9 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                             }
                         }
                         fused_pass_smem<T, KV, KK, CHK>(f, delta, v0, r0, st, st + B.rs, kcnt, sl, S, lk, hk);
-                        if (j < B.np && sl == 0) wsm[j] = dj * delta;
+                        // the residual moves by K~_b V_j delta = dres_j delta U_j (dres = d for a
+                        // Gaussian mode, |K~_b V_j| for one sampled flat)
+                        if (j < B.np && sl == 0) wsm[j] = st[2 * B.rs + 2] * delta;
                         // release the record to the producer (one arrival per warp)
                         __syncwarp();
                         mbar_arrive_lane0(empty + rp.slot, lane);
@@ -822,8 +899,26 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
             if (failed) break;
             __syncwarp();
             // exit: r~ -= U_b w (lanes split the data points; eight (WIDE: sixteen) loads in
-            // flight, eight partial sums as at entry)
+            // flight, eight partial sums as at entry; the same from the U stage)
             const T *Ut = p.pd.Ut + B.offU;
+            if (ust) {
+                for (int m = sl; m < p.M; m += S) {
+                    T a[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) a[i] = T(0);
+                    int j = 0;
+                    for (; j + 7 < B.np; j += 8) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) a[i] = m_fma(Us[(size_t)(j + i) * B.usr + m], wsm[j + i], a[i]);
+                    }
+                    for (; j < B.np; ++j) a[0] = m_fma(Us[(size_t)j * B.usr + m], wsm[j], a[0]);
+                    rsm[m] -= ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+                }
+                // release the U stage to the producer (one arrival per warp)
+                __syncwarp();
+                mbar_arrive_lane0(uempty + (rp.ug & 1u), lane);
+                ++rp.ug;
+            } else
             for (int m = sl; m < p.M; m += S) {
                 T a[8];
 #pragma unroll
@@ -904,11 +999,18 @@ __global__ void __launch_bounds__(32 * (kMaxConsumers + 1), MINB) sweep_kernel(c
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem_raw + shape.off_full);
     unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem_raw + shape.off_empty);
     unsigned char *stages = smem_raw + shape.off_stages;
+    unsigned long long *ufull = reinterpret_cast<unsigned long long *>(smem_raw + shape.off_ubar);
+    unsigned long long *uempty = ufull + 2;
+    unsigned char *ubuf = smem_raw + shape.off_ubuf;
     const int wcta = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int i = 0; i < shape.depth; ++i) {
             mbar_init(full + i, 1);
             mbar_init(empty + i, (unsigned)shape.consumers);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(ufull + i, 1);
+            mbar_init(uempty + i, (unsigned)shape.consumers);
         }
         fence_mbar_init();
         fence_proxy_async_smem();
@@ -916,7 +1018,7 @@ __global__ void __launch_bounds__(32 * (kMaxConsumers + 1), MINB) sweep_kernel(c
         rg.nsweeps = ctrl->nsweeps;
         rg.burn_in = ctrl->burn_in;
     }
-    RingPos rp{0u, 0, 0u};
+    RingPos rp{0u, 0, 0u, 0u};
     bool failed = false;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&ctrl->queue, 1);
@@ -930,9 +1032,10 @@ __global__ void __launch_bounds__(32 * (kMaxConsumers + 1), MINB) sweep_kernel(c
         }
         const SweepParams<T> &p = BATCH ? sp : p0;
         if (wcta == shape.consumers)
-            produce(p, shape, rg, full, empty, stages, rp, failed);
+            produce(p, shape, rg, full, empty, stages, ufull, uempty, ubuf, rp, failed);
         else
-            consume<T, KV, PRIOR, (MINB > 1)>(p, shape, rg, w.group, smem_raw, full, empty, stages, rp, failed);
+            consume<T, KV, PRIOR, (MINB > 1)>(p, shape, rg, w.group, smem_raw, full, empty, stages, ufull, uempty,
+                                             ubuf, rp, failed);
         __syncthreads();   // the item is finished before sp and s_item change
     }
 }

@@ -32,14 +32,18 @@ def test_noalloc_matches_the_allocating_entry_point():
     gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w)
     out = torch.empty((3, p.N), dtype=torch.float64, device="cuda")
     runs = [(48, 20, 200, 11, asm.ASM_MIXED), (96, 10, 150, 12, asm.ASM_FP64)]
-    # references first (they load every kernel the calls below use), and one
-    # call of each precision to warm up, so that the free-memory check below
-    # sees only what the two calls themselves do
+    # references first, and one round of every call the checks below make, so
+    # that each kernel -- the library's and torch's -- has been loaded before
+    # the free-memory check (a first launch loads its module into device memory)
     refs = []
     for chains, burn, sweeps, seed, prec in runs:
         gp.sample(chains, burn, sweeps, seed, precision=prec)
         refs.append(gp.average())
+        out.fill_(np.nan)
         gp.sample_noalloc(chains, burn, sweeps, seed, prec, out[0], out[1], out[2])
+        torch.cuda.synchronize()
+        _ = [out[k].cpu().numpy() for k in range(3)]
+        gp.status()
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
     # two calls in a row, the second larger than the first and in the other precision
