@@ -60,6 +60,10 @@ def _args():
     ap.add_argument("--no-tune", action="store_true", help="heuristic launch shape instead of asm_tune's")
     ap.add_argument("--batch-sweeps", type=int, default=256,
                     help="sweeps of the batching side measurement (0: skip)")
+    ap.add_argument("--largest-sweeps", type=int, default=1000,
+                    help="kept sweeps of the largest-configuration timed line (0: skip)")
+    ap.add_argument("--largest-burn", type=int, default=200)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-ASM FP64 line")
     ap.add_argument("--grid-sweeps", type=int, default=64,
                     help="sweeps per N_omega of the grid-size side measurement (0: skip)")
     ap.add_argument("--paper-sweeps", type=int, default=5000,
@@ -292,6 +296,72 @@ def grid_side(args, asm, torch, stream):
     return {"workload": "grid_sweep_fermionic_b50_Ntau400_uniform_16blocks_8192chains", "rows": rows}
 
 
+def largest_side(args, asm, torch, stream, ceil):
+    """The largest single-GPU configuration of the grid-size sweep (N_tau = 400,
+    N_omega = 2000 uniform on [-10, 10], 16 blocks, 8192 chains, noise
+    1e-5 e^{-|dtau|}) as a full timed line in the mixed path: updates/s,
+    ESS/s (binned error, min over the grid), the sweep kernel's roofline
+    against the measured ceilings, and end to end from host arrays
+    (asm_setup + asm_sample + asm_average per step)."""
+    p = W.grid_sweep_problem(2000, "uniform")
+    chains, burn, sweeps = p.chains, args.largest_burn, args.largest_sweeps
+    gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w)
+    tuned = gp.tune(chains)
+    gp.sample(chains, 0, 64, 51)
+    seed = 52
+    t = _timed(torch, stream, lambda: gp.sample(chains, burn, sweeps, seed, timing=True))
+    st = gp.status()
+    ess = gp.mc_error()["ess"]
+    elems, fmas = _ops_per_level(p)
+    lv = _level_sequence(seed, burn + sweeps, len(p.levels))
+    achieved, peak = roofline(chains * float(np.sum(elems[lv])), chains * float(np.sum(fmas[lv])),
+                              st["sweep_kernel_ms"] / 1e3, ceil, "f32")
+    upd = chains * (burn + sweeps) * p.N
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w)
+    q.sample(chains, burn, sweeps, seed + 1)
+    q.average()
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    del q
+    return {"workload": "grid_sweep_fermionic_b50_Ntau400_Nomega2000_uniform_16blocks_8192chains",
+            "chains": chains, "burn_in": burn, "sweeps": sweeps, "updates_per_s": upd / t, "seconds": t,
+            "ess_min": float(np.nanmin(ess)), "ess_per_s": float(np.nanmin(ess)) / t,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-op/s",
+                         "frac": achieved / peak if achieved else None, "kernel": "sweep_kernel<float>",
+                         "avg_launch_ms": st["sweep_kernel_ms"] / max(st["timed_launches"], 1)},
+            "e2e": {"value": upd / te, "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(a.nbytes for a in (p.K, p.G, p.C, p.w))),
+                    "d2h_bytes_per_step": int(4 * p.N * 8)},
+            "launch_shape": {"tuned": tuned, "team_lanes": st["team_lanes"],
+                             "consumers_per_cta": st["consumers_per_cta"], "ctas": st["ctas"]}}
+
+
+def plain_side(args, asm, torch, stream):
+    """The plain-ASM workload (fermionic, beta = 10, N_tau = 20, N_omega = 50,
+    global modes only, 16 chains, 1000 burn-in + 10^4 sweeps) in the plain FP64
+    path, with its binned ESS/s, beside the FP64 oracle on one host core on a
+    bounded sample of the same workload (the per-core rate)."""
+    from oracle import oracle as O
+    p = W.plain_modes_problem()
+    chains, burn, sweeps = p.chains, p.burn_in, p.sweeps
+    gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w)
+    gp.sample(chains, 0, 64, 61, precision=asm.ASM_FP64)
+    t = _timed(torch, stream, lambda: gp.sample(chains, burn, sweeps, 62, precision=asm.ASM_FP64))
+    ess = gp.mc_error()["ess"]
+    op = O.OracleProblem(p.K, p.G, p.C, p.levels)
+    t0 = time.perf_counter()
+    op.run(chains, 0, 400, seed=63, threads=1)
+    t1 = time.perf_counter() - t0
+    return {"workload": "plain_modes_fermionic_b10_Ntau20_Nomega50_16chains", "chains": chains,
+            "burn_in": burn, "sweeps": sweeps, "precision": "fp64",
+            "updates_per_s": chains * (burn + sweeps) * p.N / t, "seconds": t,
+            "ess_min": float(np.nanmin(ess)), "ess_per_s": float(np.nanmin(ess)) / t,
+            "oracle_1core": {"updates_per_s": chains * 400 * p.N / t1, "cores": 1,
+                             "sample": f"{chains} chains x 400 sweeps (FP64 oracle, one thread)"}}
+
+
 def hierarchy_side(args, asm, torch, stream):
     """The blocked-modes workload's problem under four partition schemes (Sec.
     IV): modes only (one block), components only (one point per block), the
@@ -392,8 +462,24 @@ def paper_side(args, asm, torch, stream):
                      "seconds_to_ess_1000": t * 1000.0 / ess if ess > 0 else None,
                      "max_sigma_beyond_8": float(a["mean_A"][tail].max()) if tail.any() else None})
         del gp
+    # Fig. MCsteps: step sizes Delta_s = |f(s+1) - f(s)| / |f(s)| of components, modes and
+    # blocked modes sampling on model 1 (accurate data, omega_n = 0.1 (n - 1/2), N = 40 and 120)
+    steps = []
+    for N in (40, 120):
+        p = W.paper_problem(1, 1e-3, "uniform", N, d_omega=0.1)
+        row = {"N": N, "cutoff": 0.1 * N}
+        for name, lev in (("components", [np.arange(N)]), ("modes", [[0]]),
+                          ("blocked_modes", asm.partition_hierarchy(N))):
+            gp = asm.Problem(p.K, p.G, p.C, lev, w=p.w)
+            gp.sample(chains, 0, 400, 43, step_trace=True)
+            d = gp.step_trace()[100:]
+            row[name] = {"mean_step": float(d.mean()), "median_step": float(np.median(d))}
+            del gp
+        steps.append(row)
     return {"workload": "optical_conductivity_model2_noise1e-3_beta15_60matsubara_hierarchy", "chains": chains,
-            "burn_in": burn, "sweeps": sweeps, "rows": rows}
+            "burn_in": burn, "sweeps": sweeps, "rows": rows,
+            "mc_steps": {"workload": "optical_conductivity_model1_noise1e-3_uniform_0.1", "sweeps": 400,
+                         "averaged_over": "sweeps 100-399, all chains", "rows": steps}}
 
 
 def run_reference(args):
@@ -551,6 +637,8 @@ def main():
 
     batch = batch_side(args, asm, torch, stream) if (args.batch_sweeps > 0 and rank == 0) else None
     grid = grid_side(args, asm, torch, stream) if (args.grid_sweeps > 0 and rank == 0) else None
+    largest = largest_side(args, asm, torch, stream, ceil) if (args.largest_sweeps > 0 and rank == 0) else None
+    plain = plain_side(args, asm, torch, stream) if (not args.no_plain and rank == 0) else None
     hier = hierarchy_side(args, asm, torch, stream) if (args.hierarchy_sweeps > 0 and rank == 0) else None
     paper = paper_side(args, asm, torch, stream) if (args.paper_sweeps > 0 and rank == 0) else None
     diff = diff_side(args, asm, torch, stream) if (args.diff_sweeps > 0 and rank == 0) else None
@@ -587,6 +675,8 @@ def main():
             "e2e": e2e,
             "batch": batch,
             "grid_sweep": grid,
+            "largest_config": largest,
+            "plain_asm_fp64": plain,
             "partition_schemes": hier,
             "paper_test_case": paper,
             "differentiation": diff,

@@ -62,6 +62,7 @@ enum { ASM_FP64 = 0, ASM_MIXED = 1 };   /* precision of asm_sample */
 #define ASM_SAMPLE_TIMING 2u     /* record CUDA events around every sweep-kernel launch */
 #define ASM_SAMPLE_MOMENTS 4u    /* accumulate the snapshot moments asm_backward needs */
 #define ASM_SAMPLE_REFRESH_FP64 8u  /* ASM_MIXED: refresh residuals on FP64 CUDA cores, not 3xTF32 tensor cores */
+#define ASM_SAMPLE_STEP_TRACE 16u   /* record the step sizes of every sweep (asm_step_trace) */
 #define ASM_SNAPSHOT_EVERY 8     /* kept sweeps between snapshots of all chains */
 
 /* Environment variables the library reads (testing and tuning only; no result
@@ -71,8 +72,12 @@ enum { ASM_FP64 = 0, ASM_MIXED = 1 };   /* precision of asm_sample */
  *                          asm_setup (asm_tune replaces it);
  *   ASM_CONSUMERS_PER_CTA  1..7: chain warps per CTA of every sweep launch
  *                          (takes precedence over the heuristic and asm_tune);
- *   ASM_RING_DEPTH         2..16: stages of the move-record ring (default: as
- *                          many as shared memory holds, at most 16). */
+ *   ASM_RING_DEPTH         2..48: stages of the move-record ring (default: as
+ *                          many as shared memory holds, at most 48);
+ *   ASM_RECORDS_PER_STAGE  1..8: consecutive move records per ring stage
+ *                          (default 4: one barrier wait and release per stage);
+ *   ASM_NO_U_STAGE         set: the block projections read U from global memory
+ *                          instead of a shared-memory stage. */
 
 typedef struct asm_problem asm_problem;  /* opaque, library-owned */
 
@@ -339,6 +344,17 @@ enum {
     ASM_CEIL_DMNMX = 8, ASM_CEIL_I64MNMX = 9, ASM_CEIL_KINDS = 10
 };
 int asm_measure_ceiling(int kind, double target_ms, double *ops_per_s, double *sm_mhz, double *ms);
+
+/* Step sizes of the sampler (Sec. IV.D, Fig. MCsteps): delta[s] = the mean over
+ * the chains of problem k of Delta_s = |f(s+1) - f(s)| / |f(s)|, f(s) the
+ * chain's state before sweep s counted from the start of its chains, for the
+ * first min(sweeps done, 4096, max_sweeps) sweeps; *n_sweeps receives that
+ * count.  Recorded by every asm_sample that carries ASM_SAMPLE_STEP_TRACE
+ * (sweeps run without the flag leave their entries at 0; the norms are summed
+ * in the chain state's precision).  Synchronises.  The trace shows how far one
+ * Monte Carlo step moves the model, the paper's measure of the efficiency of
+ * components, modes and blocked modes sampling. */
+int asm_step_trace(asm_problem *p, int k, double *delta, int max_sweeps, int *n_sweeps);
 
 /* Identities that key the random numbers (Philox counter words): problem_id
  * (default 0) and the global id of local chain 0 (default 0).  Chains are

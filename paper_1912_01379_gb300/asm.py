@@ -21,6 +21,7 @@ ASM_SAMPLE_CONTINUE = 1
 ASM_SAMPLE_TIMING = 2
 ASM_SAMPLE_MOMENTS = 4
 ASM_SAMPLE_REFRESH_FP64 = 8
+ASM_SAMPLE_STEP_TRACE = 16
 ASM_FLAG_TEST_STALL = 0x80000000   # asm_desc flag: failure-path tests only
 ASM_ERR_TIMEOUT = -10
 ASM_SNAPSHOT_EVERY = 8
@@ -56,7 +57,8 @@ class asm_stats(ct.Structure):
 EXPORTS = ["asm_setup", "asm_workspace_bytes", "asm_sample", "asm_average", "asm_chain_state",
            "asm_status", "asm_destroy", "asm_error_string", "asm_sample_noalloc", "asm_set_stream_ids",
            "asm_checkpoint", "asm_restore", "asm_backward", "asm_setup_batch", "asm_problem_count",
-           "asm_average_at", "asm_tune", "asm_partition_hierarchy", "asm_mc_error", "asm_measure_ceiling"]
+           "asm_average_at", "asm_tune", "asm_partition_hierarchy", "asm_mc_error", "asm_measure_ceiling",
+           "asm_step_trace"]
 # instruction mixes of asm_measure_ceiling
 CEILING_KINDS = {"pass_f32": 0, "pass_f32_smem": 1, "ffma": 2, "fmnmx": 3, "imnmx": 4, "pass_f64": 5,
                  "pass_f64_smem": 6, "dfma": 7, "dmnmx": 8, "i64mnmx": 9}
@@ -123,6 +125,8 @@ def load(build_if_missing: bool = True):
     L.asm_mc_error.restype = ct.c_int
     L.asm_measure_ceiling.argtypes = [ct.c_int, ct.c_double, _dp, _dp, _dp]
     L.asm_measure_ceiling.restype = ct.c_int
+    L.asm_step_trace.argtypes = [ct.c_void_p, ct.c_int, _dp, ct.c_int, _ip]
+    L.asm_step_trace.restype = ct.c_int
     _lib = L
     return L
 
@@ -246,13 +250,14 @@ class _Handle:
         return torch, workspace
 
     def sample(self, chains, burn_in, sweeps, seed, precision=ASM_MIXED, cont=False, stream=None,
-               workspace=None, timing=False, moments=False, refresh_fp64=False):
+               workspace=None, timing=False, moments=False, refresh_fp64=False, step_trace=False):
         """asm_sample on a torch workspace (allocated here unless given) and the
         current torch stream (or `stream`)."""
         torch, workspace = self._workspace(chains, precision, workspace)
         s = stream if stream is not None else torch.cuda.current_stream()
         flags = ((ASM_SAMPLE_CONTINUE if cont else 0) | (ASM_SAMPLE_TIMING if timing else 0) |
-                 (ASM_SAMPLE_MOMENTS if moments else 0) | (ASM_SAMPLE_REFRESH_FP64 if refresh_fp64 else 0))
+                 (ASM_SAMPLE_MOMENTS if moments else 0) | (ASM_SAMPLE_REFRESH_FP64 if refresh_fp64 else 0) |
+                 (ASM_SAMPLE_STEP_TRACE if step_trace else 0))
         _check(load().asm_sample(self._h, chains, burn_in, sweeps, ct.c_uint64(seed), precision, flags,
                                  ct.c_void_p(workspace.data_ptr()), workspace.numel(),
                                  ct.c_void_p(s.cuda_stream)), "asm_sample")
@@ -284,6 +289,14 @@ class _Handle:
         _check(load().asm_mc_error(self._h, k, _dptr(ess), _dptr(sem), _dptr(lv), bins.ctypes.data_as(_ip)),
                "asm_mc_error")
         return {"ess": ess, "sem_fbar": sem, "sigma2_levels": lv, "bins_per_chain": bins}
+
+    def step_trace(self, k=0, max_sweeps=4096):
+        """asm_step_trace: mean over the chains of |f(s+1) - f(s)| / |f(s)| per sweep s
+        (sweeps sampled with step_trace=True)."""
+        out = np.zeros(max_sweeps)
+        n = ct.c_int(0)
+        _check(load().asm_step_trace(self._h, k, _dptr(out), max_sweeps, ct.byref(n)), "asm_step_trace")
+        return out[:n.value]
 
     def status(self):
         st = asm_stats()

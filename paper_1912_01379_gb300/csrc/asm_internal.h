@@ -84,6 +84,10 @@ struct SweepParams {
     double *rref;
     // gamma prior: a_n - 1 per grid point (nullptr: flat)
     const T *prior_am1;
+    // step-size trace (nullptr: off): sum over chains of |f(s+1) - f(s)| / |f(s)| for
+    // the absolute sweeps s < trace_cap
+    double *steptrace;
+    int trace_cap;
 };
 
 // What every problem of one launch shares: the CTA shape and the
@@ -96,7 +100,8 @@ struct LaunchShape {
     int consumers;                    // consumer warps per CTA (the producer is one more)
     int depth;                        // stages in the ring
     int off_full, off_empty, off_stages;  // byte offsets in dynamic shared memory
-    int stage_bytes;                  // bytes per stage (>= the largest record)
+    int stage_bytes;                  // bytes per stage (>= rps of the largest records)
+    int rps;                          // move records per stage (consecutive moves of one block)
     int cpad;                         // shared-memory stride of the c/w buffers (>= max np)
     int mpad;                         // shared-memory stride of the residual (>= max M)
     int n_items;                      // (problem, chain group) work items
@@ -183,12 +188,16 @@ constexpr int kWaitLimit = 1 << 22;
 // levels (bins of 64 ... 8192 sweeps).
 constexpr int kBinSweeps = 64;
 constexpr int kBinLevels = 8;
+// Sweeps from the chains' start whose step size the trace records.
+constexpr int kStepTraceMax = 4096;
 // Consumer warps per CTA: at most 7, so that a CTA (consumers + the producer)
 // has at most 8 warps, two per SM sub-partition, and a thread may hold up to
 // 255 registers (9 warps would put three on one sub-partition: 168).
 constexpr int kMaxConsumers = 7;
 // Deepest ring of move records (stages) a launch may use.
 constexpr int kMaxRingDepth = 48;
+// Move records per ring stage (one barrier wait and one release per stage).
+constexpr int kRecordsPerStage = 4;
 constexpr int kMaxKvF32 = 16;   // 64 floats per lane
 constexpr int kMaxKvF64 = 32;   // 64 doubles per lane
 

@@ -320,6 +320,7 @@ struct WsLayout {
     size_t shift, kshift, D;                // centring of the snapshots
     size_t S1p, bpend, bacc1, bacc2, bcount; // binning of the Monte Carlo error
     size_t fref, rref;                       // reference state of the tensor-core refresh
+    size_t steptrace;                        // step-size trace (kStepTraceMax sweeps)
     size_t total;
     int ldF, ldR;
 };
@@ -381,14 +382,15 @@ struct asm_problem {
     struct GraphKey {
         const void *ws_all = nullptr;
         int chains = 0, precision = -1, kv = 0, ctas = 0, S = 0, consumers = 0, depth = 0, n_items = 0, minb = 0,
-            ubytes = 0;
+            ubytes = 0, rps = 0;
         size_t refresh_smem = 0;
         unsigned long long seed = 0, problem_id = 0, chain_offset = 0;
         bool operator==(const GraphKey &o) const
         {
             return ws_all == o.ws_all && chains == o.chains && precision == o.precision && kv == o.kv &&
                    ctas == o.ctas && S == o.S && consumers == o.consumers && depth == o.depth &&
-                   n_items == o.n_items && minb == o.minb && ubytes == o.ubytes && refresh_smem == o.refresh_smem &&
+                   n_items == o.n_items && minb == o.minb && ubytes == o.ubytes && rps == o.rps &&
+                   refresh_smem == o.refresh_smem &&
                    seed == o.seed &&
                    problem_id == o.problem_id && chain_offset == o.chain_offset;
         }
@@ -397,6 +399,7 @@ struct asm_problem {
     bool refresh_fp64 = false;   // mixed path: FP64 CUDA-core refresh instead of the tensor cores
     int last_team = 0, last_consumers = 0, last_ctas = 0, last_items = 0, last_minb = 0;   // last sweep launch
     bool no_graph = false;    // direct launches only (the allocation-free entry point)
+    bool trace = false;       // ASM_SAMPLE_STEP_TRACE: the step-size trace of every sweep
     bool test_stall = false;  // ASM_FLAG_TEST_STALL: the failure path under test
     // launch bookkeeping
     long long sweep_launches = 0, other_launches = 0, timed_launches = 0;
@@ -439,6 +442,7 @@ WsLayout ws_layout(const asm_problem *p, int chains, int precision)
     L.bcount = off; off = align_up(off + (size_t)chains * 4, 256);
     L.fref = off; off = align_up(off + N * 4, 256);
     L.rref = off; off = align_up(off + (size_t)p->M * 8, 256);
+    L.steptrace = off; off = align_up(off + (size_t)kStepTraceMax * 8, 256);
     L.total = off;
     return L;
 }
@@ -881,6 +885,8 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.f0 = p->f0;
     sp.fref = (float *)(ws + L.fref);
     sp.rref = (double *)(ws + L.rref);
+    sp.steptrace = p->trace ? (double *)(ws + L.steptrace) : nullptr;
+    sp.trace_cap = kStepTraceMax;
     return sp;
 }
 
@@ -910,7 +916,7 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
     sh.wait_limit = kWaitLimit;
     sh.stall = 0;
     constexpr int kSMs = 152;
-    constexpr int kMinRing = 8;   // the U stages may not squeeze the record ring below this depth
+    constexpr int kMinRingRecords = 8;   // the U stages may not squeeze the ring below this many records
     const int TW = 32 / S;
     const int prec = sizeof(T) == 8 ? ASM_FP64 : ASM_MIXED;
     sh.S = S;
@@ -924,7 +930,13 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
         const int c = std::atoi(e);
         if (c >= 1 && c <= kMaxConsumers) consumers = c;
     }
-    sh.stage_bytes = (int)align_up((size_t)max_rec * sizeof(T), 128);
+    sh.rps = kRecordsPerStage;
+    if (const char *e = std::getenv("ASM_RECORDS_PER_STAGE")) {   // tuning override
+        const int r = std::atoi(e);
+        if (r >= 1 && r <= 8) sh.rps = r;
+    }
+    sh.stage_bytes = (int)align_up((size_t)sh.rps * max_rec * sizeof(T), 128);
+    const int kMinRing = std::max(2, (kMinRingRecords + sh.rps - 1) / sh.rps);
     // per-team state, then the ring's barriers (full, empty: 8 bytes per stage each), the
     // U stages' barriers (4 x 8 bytes, padded to 128) and the U stages
     constexpr int kBarBytes = 8 * kMaxRingDepth;
@@ -1166,7 +1178,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
         refresh_all_kernel<T><<<n_refresh, 128, rsmem, st>>>(d_probs, chains, 1);
         return cudaGetLastError();
     };
-    bool graphs = !h->timing && !h->moments && !h->no_graph;
+    bool graphs = !h->timing && !h->moments && !h->no_graph && !h->trace;
     if (graphs) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) return ASM_ERR_CUDA;
@@ -1188,6 +1200,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             key.n_items = sh.n_items;
             key.minb = sh.minb + 4 * sh.prior + 8 * sh.stall;
             key.ubytes = sh.ubytes;
+            key.rps = sh.rps;
             key.refresh_smem = tc ? refresh_tc_smem(max_bn) + 1 : rsmem;
             key.seed = p0.seed;   // by value in a single problem's launch
             key.problem_id = p0.problem_id;
@@ -1275,6 +1288,9 @@ int init_chains(asm_problem *p, const WsLayout &L, int chains)
     if (cudaMemsetAsync(ws + L.Sff, 0, L.Y - L.Sff, p->stream) != cudaSuccess) return ASM_ERR_CUDA;
     // binning state starts empty
     if (cudaMemsetAsync(ws + L.S1p, 0, L.bcount + (size_t)chains * 4 - L.S1p, p->stream) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    // and so does the step-size trace
+    if (cudaMemsetAsync(ws + L.steptrace, 0, (size_t)kStepTraceMax * 8, p->stream) != cudaSuccess)
         return ASM_ERR_CUDA;
     p->nsnap = 0;
     if (const int rc = refresh_smem(refresh_kernel<T>, sizeof(double) * p->N); rc != ASM_OK) return rc;
@@ -1670,7 +1686,8 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
 {
     if (!p || chains < 1 || burn_in < 0 || sweeps < 0) return ASM_ERR_ARG;
     if (precision != ASM_FP64 && precision != ASM_MIXED) return ASM_ERR_ARG;
-    if (flags & ~(ASM_SAMPLE_CONTINUE | ASM_SAMPLE_TIMING | ASM_SAMPLE_MOMENTS | ASM_SAMPLE_REFRESH_FP64))
+    if (flags & ~(ASM_SAMPLE_CONTINUE | ASM_SAMPLE_TIMING | ASM_SAMPLE_MOMENTS | ASM_SAMPLE_REFRESH_FP64 |
+                  ASM_SAMPLE_STEP_TRACE))
         return ASM_ERR_ARG;
     const bool moments = (flags & ASM_SAMPLE_MOMENTS) != 0;
     if (moments && !p->kids.empty()) return ASM_ERR_ARG;   // backward moments: single problems
@@ -1684,6 +1701,8 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
     bind_workspace(p, d_workspace, workspace_bytes, RL, (cudaStream_t)stream);
     p->timing = (flags & ASM_SAMPLE_TIMING) != 0;
     p->refresh_fp64 = (flags & ASM_SAMPLE_REFRESH_FP64) != 0;
+    p->trace = (flags & ASM_SAMPLE_STEP_TRACE) != 0;
+    for (asm_problem *u : p->kids) u->trace = p->trace;
     int rc;
     if (!cont) {
         rc = start_chains(p, chains, precision, seed, moments);
@@ -2026,6 +2045,7 @@ int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, ui
     bind_workspace(p, scratch, ASM_NOALLOC_SCRATCH_BYTES, RL, (cudaStream_t)stream);
     p->timing = false;
     p->refresh_fp64 = false;   // the mixed path refreshes on the tensor cores, whatever ran before
+    p->trace = false;
     // counters, sums and residuals are zeroed and the chains re-started here
     rc = start_chains(p, chains, precision, seed, false);
     if (rc != ASM_OK) return rc;
@@ -2043,6 +2063,23 @@ int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, ui
                                                              (double)sweeps, d_mean_fbar, d_sem2_fbar, d_m2_fbar);
     ++p->other_launches;
     return cudaGetLastError() == cudaSuccess ? ASM_OK : ASM_ERR_CUDA;
+}
+
+int asm_step_trace(asm_problem *p, int k, double *delta, int max_sweeps, int *n_sweeps)
+{
+    if (!p || !delta || !n_sweeps || max_sweeps < 0 || k < 0 || k >= asm_problem_count(p)) return ASM_ERR_ARG;
+    asm_problem *u = p->kids.empty() ? p : p->kids[(size_t)k];
+    if (!p->have_run || !u->have_run) return ASM_ERR_STATE;
+    const int n = (int)std::min<long long>({u->sweeps_done, (long long)kStepTraceMax, (long long)max_sweeps});
+    const WsLayout L = ws_layout(u, u->chains, u->precision);
+    std::vector<double> h((size_t)std::max(n, 1));
+    if (n > 0 && (cudaMemcpyAsync(h.data(), (const char *)u->ws + L.steptrace, sizeof(double) * n,
+                                  cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+                  cudaStreamSynchronize(p->stream) != cudaSuccess))
+        return ASM_ERR_CUDA;
+    for (int s = 0; s < n; ++s) delta[s] = h[s] / u->chains;
+    *n_sweeps = n;
+    return ASM_OK;
 }
 
 int asm_set_stream_ids(asm_problem *p, uint64_t problem_id, uint64_t chain_offset)

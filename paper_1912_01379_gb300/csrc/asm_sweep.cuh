@@ -501,7 +501,7 @@ struct SweepRange {
 // A warp's position in the record ring: records seen (g), stage and phase
 // (kept incrementally: no division per move).
 struct RingPos {
-    unsigned g;             // records in this launch (< 2^32: one launch is at most 64 sweeps)
+    unsigned g;             // stages in this launch (< 2^32: one launch is at most 64 sweeps)
     int slot;
     unsigned phase;
     unsigned ug;            // block visits whose U went through the two U stages
@@ -549,9 +549,9 @@ __device__ __forceinline__ void cursor_start_sweep(MoveCursor &c, const SweepPar
 }
 
 template <class T>
-__device__ __forceinline__ void cursor_advance(MoveCursor &c, const SweepParams<T> &p)
+__device__ __forceinline__ void cursor_advance(MoveCursor &c, const SweepParams<T> &p, int n = 1)
 {
-    if (++c.j < c.B.n) return;
+    if ((c.j += n) < c.B.n) return;
     c.j = 0;
     if (++c.bi < c.nb) {
         c.B = c.bd[c.bi];
@@ -580,9 +580,9 @@ __device__ __forceinline__ void mbar_arrive_lane0(unsigned long long *bar, int l
 }
 
 // --------------------------------------------------------------------------
-// The producer warp: one bulk copy per move of the item into the ring, after
-// every consumer warp has released the slot's previous record.  The ring
-// position runs on across the CTA's items.
+// The producer warp: one bulk copy per stage of up to sh.rps consecutive move
+// records of one block into the ring, after every consumer warp has released
+// the slot's previous stage.  The ring position runs on across the CTA's items.
 // --------------------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchShape &sh, const SweepRange &rg,
@@ -612,17 +612,18 @@ __device__ __forceinline__ void produce(const SweepParams<T> &p, const LaunchSha
             bulk_g2s(ubuf + (size_t)us * sh.ubytes, p.pd.Us + c.B.offUs, ubytes, ufull + us);
             ++rp.ug;
         }
-        // the slot's previous record (phase ^ 1) must have been released
+        // the slot's previous stage (phase ^ 1) must have been released
         if (rp.g >= (unsigned)D && !mbar_wait(empty + rp.slot, rp.phase ^ 1u, sh.wait_limit)) {
             failed = true;
             break;
         }
-        const unsigned bytes = (unsigned)(c.B.recstride * sizeof(T));
+        const int nrec = min(sh.rps, c.B.n - c.j);   // records of this stage (a stage stays in its block)
+        const unsigned bytes = (unsigned)(nrec * c.B.recstride * sizeof(T));
         mbar_expect_tx(full + rp.slot, bytes);
         bulk_g2s(stages + (size_t)rp.slot * sh.stage_bytes, p.pd.rec + c.B.offRec + (size_t)c.j * c.B.recstride,
                  bytes, full + rp.slot);
         ring_next(rp, D);
-        cursor_advance(c, p);
+        cursor_advance(c, p, nrec);
     }
     if (failed) {
         // the copies already issued must land before the CTA may exit
@@ -679,6 +680,7 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
 
     T f[KV][VEC];
     unsigned n_deg = 0, n_zero = 0, n_bad = 0, n_rej = 0;   // per launch: at most 64 sweeps of moves
+    const bool trace = p.steptrace != nullptr;   // step-size trace of Fig. MCsteps (diagnostic)
     int capped = 0;
     const long long s_end = rg.sweep0 + rg.nsweeps;
     for (long long s = rg.sweep0; s < s_end && !failed; ++s) {
@@ -688,6 +690,7 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
         int win = 0, win_end = -1;  // window [win, win_end) of moves whose uniforms are in usm
         const int nb = p.level_nblocks[level];
         const BlockDesc *bd = p.blocks + p.level_first[level];
+        T sd2 = T(0), sf2 = T(0);   // this lane's |f(s+1) - f(s)|^2 and |f(s)|^2 (trace only)
 
         for (int bi = 0; bi < nb && !failed; ++bi) {
             const BlockDesc B = bd[bi];
@@ -771,6 +774,8 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                 constexpr int KC = decltype(chunks)::value;   // 0: kcnt chunks, each tested
                 constexpr int KK = KC ? KC : KV;
                 constexpr bool CHK = KC == 0;
+                int jr = 0;                        // record of move j within its ring stage
+                const T *stb = nullptr;            // the stage holding move j's record
                 for (int j = 0; j < B.n && !failed;) {
                     // uniform of move t: word t%4 of Philox(ctr = {t/4, s, q, problem}); the 4S
                     // uniforms of a window come from one Philox call per lane (lane sl: ctr
@@ -807,16 +812,20 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                         const T cj = j < B.np ? csm[j] : T(0);
                         const int t = B.start + j;
                         const T u = usm[t - win];
-                        // this move's record: usually landed long ago (one test, one vote)
-                        bool ok = mbar_test_wait(full + rp.slot, rp.phase);
-                        if (__any_sync(0xffffffffu, !ok)) {
-                            ok = ok || mbar_wait(full + rp.slot, rp.phase, sh.wait_limit);
-                            if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
-                                failed = true;
-                                break;
+                        // the stage of this move's record: usually landed long ago (one test, one
+                        // vote per stage of sh.rps moves)
+                        if (jr == 0) {
+                            bool ok = mbar_test_wait(full + rp.slot, rp.phase);
+                            if (__any_sync(0xffffffffu, !ok)) {
+                                ok = ok || mbar_wait(full + rp.slot, rp.phase, sh.wait_limit);
+                                if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
+                                    failed = true;
+                                    break;
+                                }
                             }
+                            stb = reinterpret_cast<const T *>(stages + (size_t)rp.slot * sh.stage_bytes);
                         }
-                        const T *st = reinterpret_cast<const T *>(stages + (size_t)rp.slot * sh.stage_bytes);
+                        const T *st = stb + (size_t)jr * B.recstride;
                         const T dj = st[2 * B.rs], ij = st[2 * B.rs + 1];
                         T v0[VEC], r0[VEC];   // chunk 0 of the pass: independent of the draw, loaded first
                         lds_v(st + VEC * sl, v0);
@@ -881,10 +890,15 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                         // the residual moves by K~_b V_j delta = dres_j delta U_j (dres = d for a
                         // Gaussian mode, |K~_b V_j| for one sampled flat)
                         if (j < B.np && sl == 0) wsm[j] = st[2 * B.rs + 2] * delta;
-                        // release the record to the producer (one arrival per warp)
-                        __syncwarp();
-                        mbar_arrive_lane0(empty + rp.slot, lane);
-                        ring_next(rp, D);
+                        // release the stage to the producer after its last record (one arrival per warp)
+                        if (jr + 1 == sh.rps || j + 1 == B.n) {
+                            __syncwarp();
+                            mbar_arrive_lane0(empty + rp.slot, lane);
+                            ring_next(rp, D);
+                            jr = 0;
+                        } else {
+                            ++jr;
+                        }
                     }
                 }
             };
@@ -951,6 +965,11 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     const int nl = VEC * (k * S + sl) + v;
                     if (active && k < kcnt && nl < B.n) {
                         const int n = B.start + nl;
+                        if (trace) {
+                            const T old = Fq[n], dlt = f[k][v] - old;
+                            sd2 = m_fma(dlt, dlt, sd2);
+                            sf2 = m_fma(old, old, sf2);
+                        }
                         Fq[n] = f[k][v];
                         if (keep) {
                             const double x = (double)f[k][v];
@@ -960,6 +979,14 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                     }
                 }
             __syncwarp();
+        }
+        if (trace && !failed) {   // Delta_s = |f(s+1) - f(s)| / |f(s)| of this chain, summed over chains
+            for (int off = 1; off < S; off <<= 1) {
+                sd2 += __shfl_xor_sync(0xffffffffu, sd2, off);
+                sf2 += __shfl_xor_sync(0xffffffffu, sf2, off);
+            }
+            if (active && sl == 0 && s < p.trace_cap && sf2 > T(0))
+                atomicAdd(p.steptrace + s, sqrt((double)sd2 / (double)sf2));
         }
     }
     if (failed) {

@@ -1,0 +1,96 @@
+"""The step-size trace of Fig. MCsteps (Sec. IV.D): Delta_s = |f(s+1) - f(s)| /
+|f(s)| per sweep, averaged over the chains, recorded on the device
+(asm_sample with ASM_SAMPLE_STEP_TRACE, read by asm_step_trace).
+
+* FP64 with the oracle's singular vectors and random numbers: the trace equals
+  the one computed from the oracle's own states, sweep by sweep, within the
+  step-by-step tolerance over the reproducible window.
+* The paper's comparison on its model 1 (accurate data, uniform grid
+  omega_n = 0.1 (n - 1/2) with N = 40 and 120): blocked modes sampling moves
+  the model much further per step than components sampling at both cutoffs,
+  and further than modes sampling; in the oracle's mode basis the GPU's mean
+  step agrees with the oracle's within the spread of the chains.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1912_01379_gb300 import asm
+from paper_1912_01379_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STEP_RTOL = 1e-9
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+    torch.cuda.synchronize()
+
+
+def _oracle_deltas(op, chains, sweeps, seed, f0):
+    tr = op.run(chains, 0, sweeps, seed=seed, trace_chains=chains, f_start=f0)["trace"]
+    full = np.concatenate([np.broadcast_to(f0, (chains, 1, len(f0))), tr], axis=1)
+    d = np.linalg.norm(np.diff(full, axis=1), axis=2) / np.linalg.norm(full[:, :-1], axis=2)
+    return d, tr
+
+
+@pytest.mark.parametrize("case", ["plain_modes", "ragged_levels"])
+def test_trace_matches_the_oracle_step_by_step(case):
+    if case == "plain_modes":
+        p, seed = W.plain_modes_problem(), 1234
+    else:
+        p, seed = W.small_problem(30, 150, seed=21, levels=[[0], [0, 37, 87], np.arange(150)[::10],
+                                                             np.arange(150)]), 1235
+    op = O.OracleProblem(p.K, p.G, p.C, p.levels)
+    dec = op.decomposition()
+    chains, sweeps = 7, 4
+    f0 = op.initial_f()
+    d, tr = _oracle_deltas(op, chains, sweeps, seed, f0)
+    # reproducible window: the oracle against itself from a start one ulp away
+    tb = op.run(chains, 0, sweeps, seed=seed, trace_chains=chains, f_start=f0 * (1 + 2.0 ** -52))["trace"]
+    sens = (np.abs(tr - tb) / np.abs(tr).max(axis=2, keepdims=True)).max(axis=(0, 2))
+    window = max(1, int(np.argmax(np.append(sens, np.inf) > 1e-11)))
+    gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w, factors=dec)
+    gp.sample(chains, 0, sweeps, seed, precision=asm.ASM_FP64, step_trace=True)
+    got = gp.step_trace()
+    assert len(got) == sweeps
+    want = d.mean(axis=0)
+    assert np.allclose(got[:window], want[:window], rtol=STEP_RTOL, atol=0), (got, want, window)
+    assert np.all(got > 0)
+    # sweeps run without the flag leave zeros; a continuation with it records its sweeps
+    gp.sample(chains, 0, 2, seed, precision=asm.ASM_FP64, cont=True)
+    gp.sample(chains, 0, 1, seed, precision=asm.ASM_FP64, cont=True, step_trace=True)
+    got = gp.step_trace()
+    assert len(got) == sweeps + 3 and np.all(got[sweeps:sweeps + 2] == 0) and got[-1] > 0
+
+
+def _mean_steps(p, levels, chains, sweeps, seed):
+    gp = asm.Problem(p.K, p.G, p.C, levels, w=p.w)
+    gp.sample(chains, 0, sweeps, seed, precision=asm.ASM_MIXED, step_trace=True)
+    return gp.step_trace()
+
+
+@pytest.mark.parametrize("N", [40, 120])
+def test_blocked_modes_take_the_largest_steps(N):
+    p = W.paper_problem(1, 1e-3, "uniform", N, d_omega=0.1)
+    schemes = {"components": [np.arange(N)], "modes": [[0]], "blocked": asm.partition_hierarchy(N)}
+    chains, sweeps = 512, 400
+    mean = {k: _mean_steps(p, lev, chains, sweeps, 7)[100:].mean() for k, lev in schemes.items()}
+    assert mean["blocked"] > 4 * mean["components"], mean
+    assert mean["blocked"] > 1.5 * mean["modes"], mean
+    # the oracle's steps agree with the GPU's in the same mode basis (the step size of a
+    # sweep depends on the basis chosen within degenerate and null subspaces, which
+    # cuSOLVER and the oracle's Jacobi SVD choose differently)
+    op = O.OracleProblem(p.K, p.G, p.C, schemes["blocked"])
+    gp = asm.Problem(p.K, p.G, p.C, schemes["blocked"], w=p.w, factors=op.decomposition())
+    gp.sample(chains, 0, sweeps, 7, precision=asm.ASM_MIXED, step_trace=True)
+    gpu = gp.step_trace()[100:].mean()
+    d, _ = _oracle_deltas(op, 32, sweeps, 8, op.initial_f())
+    per_chain = d[:, 100:].mean(axis=1)
+    sem = per_chain.std(ddof=1) / np.sqrt(len(per_chain))
+    assert abs(per_chain.mean() - gpu) <= 4.5 * sem, (per_chain.mean(), gpu, sem)
