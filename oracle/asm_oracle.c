@@ -507,7 +507,8 @@ struct ora_problem {
     double *Kt, *gt;     /* whitened kernel (M x N row-major) and data */
     double *prior_am1;   /* a_n - 1 of the gamma prior prod f_n^(a_n - 1) (Eq. compat), NULL: flat */
     int flat_exp;        /* R2: sign-changing modes with d <= d_1 max(M,n) 2^-flat_exp are flat */
-    int mu_jitter;       /* test of rounding sensitivity: every conditional mean moved by one ulp */
+    int jitter;          /* test of rounding sensitivity: 0 off, else every conditional mean and
+                          * interval end moved by one rounding at unit roundoff 2^-jitter */
 };
 
 void ora_free(ora_problem *p)
@@ -629,7 +630,7 @@ ora_problem *ora_setup(int M, int N, const double *K, const double *G, const dou
     return ora_setup_ex(M, N, K, G, C, n_levels, level_nblocks, block_start, 40, err);
 }
 
-void ora_set_mu_jitter(ora_problem *p, int on) { p->mu_jitter = on ? 1 : 0; }
+void ora_set_jitter(ora_problem *p, int unit_exp) { p->jitter = (unit_exp >= 1 && unit_exp <= 60) ? unit_exp : 0; }
 
 void ora_sizes(const ora_problem *p, long *n_d, long *n_V, long *n_U)
 {
@@ -815,7 +816,7 @@ static void ora_chain(const ora_problem *p, uint64_t q, double *f, long sweep0, 
     int M = p->M, N = p->N;
     double *gp = (double *)malloc(sizeof(double) * M);
     double *h = (double *)malloc(sizeof(double) * (M > 0 ? M : 1));
-    double *habs = p->mu_jitter ? (double *)malloc(sizeof(double) * (M > 0 ? M : 1)) : NULL;
+    double *habs = p->jitter ? (double *)malloc(sizeof(double) * (M > 0 ? M : 1)) : NULL;
     const uint64_t key[2] = {seed, 0};
     long viol = 0, degen = 0, flat = 0;
     int capped = 0;
@@ -836,8 +837,12 @@ static void ora_chain(const ora_problem *p, uint64_t q, double *f, long sweep0, 
                 double mu, sigma, lo, hi, delta, mu_scale;
                 ora_mode_conditional(b, j, f, h, habs, &mu, &sigma, &mu_scale);
                 ora_bounds(b, j, f, &lo, &hi);
-                if (p->mu_jitter && sigma > 0.0)   /* a rounding of the terms of mu, up or down by a bit of the move's word */
-                    mu += ((w[t & 3] & 2) ? 1.0 : -1.0) * 0x1p-52 * mu_scale;
+                if (p->jitter) {   /* one rounding each, up or down by bits 1-3 of the move's word */
+                    const double ulp = ldexp(1.0, -p->jitter);
+                    if (sigma > 0.0) mu += ((w[t & 3] & 2) ? 1.0 : -1.0) * ulp * mu_scale;
+                    if (isfinite(lo)) lo += ((w[t & 3] & 4) ? 1.0 : -1.0) * ulp * fabs(lo);
+                    if (isfinite(hi)) hi += ((w[t & 3] & 8) ? 1.0 : -1.0) * ulp * fabs(hi);
+                }
                 if (!(hi > lo)) {
                     delta = 0.0;
                     ++degen;

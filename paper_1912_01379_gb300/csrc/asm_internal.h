@@ -88,6 +88,9 @@ struct SweepParams {
     // the absolute sweeps s < trace_cap
     double *steptrace;
     int trace_cap;
+    // FP32 chain state: the sums of f and f^2 over one launch's kept sweeps (FP32,
+    // chains x ldF) where shared memory cannot hold them; added to S1, S2 per launch
+    float *P1, *P2;
 };
 
 // What every problem of one launch shares: the CTA shape and the
@@ -104,6 +107,9 @@ struct LaunchShape {
     int rps;                          // move records per stage (consecutive moves of one block)
     int cpad;                         // shared-memory stride of the c/w buffers (>= max np)
     int mpad;                         // shared-memory stride of the residual (>= max M)
+    int npad;                         // shared-memory sums of the kept sweeps per team (>= max N;
+                                      // 0: the kept sweeps are added to the FP64 sums directly)
+    int team_words;                   // shared-memory elements per team: 2 cpad + mpad + 8 S + 2 npad
     int n_items;                      // (problem, chain group) work items
     int minb;                         // register budget: 1 or 2 CTAs per SM
     int prior;                        // 1: kernels with the gamma prior's acceptance step

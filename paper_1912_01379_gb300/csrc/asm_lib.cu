@@ -191,21 +191,23 @@ __global__ void bin_reduce_kernel(const double *__restrict__ acc1, const double 
 }
 
 // Per grid point: mean over chains and kept sweeps, the spread of the chain
-// means (two passes) and the second moment.
-__global__ void reduce_kernel(const double *S1, const double *S2, int chains, int N, double kept,
-                              double *mean, double *semsq, double *m2)
+// means (two passes) and the second moment.  P1, P2 (FP32 chain state; else
+// null): the kept-sweep sums of a 64-sweep block still open, added here.
+__global__ void reduce_kernel(const double *S1, const double *S2, const float *P1, const float *P2, int ldP,
+                              int chains, int N, double kept, double *mean, double *semsq, double *m2)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
+    auto s1 = [&](int q) { return S1[(size_t)q * N + n] + (P1 ? (double)P1[(size_t)q * ldP + n] : 0.0); };
     double a = 0.0, b = 0.0;
     for (int q = 0; q < chains; ++q) {
-        a += S1[(size_t)q * N + n];
-        b += S2[(size_t)q * N + n];
+        a += s1(q);
+        b += S2[(size_t)q * N + n] + (P2 ? (double)P2[(size_t)q * ldP + n] : 0.0);
     }
     const double mu = a / (chains * kept);
     double v = 0.0;
     for (int q = 0; q < chains; ++q) {
-        const double d = S1[(size_t)q * N + n] / kept - mu;
+        const double d = s1(q) / kept - mu;
         v += d * d;
     }
     mean[n] = mu;
@@ -321,6 +323,7 @@ struct WsLayout {
     size_t S1p, bpend, bacc1, bacc2, bcount; // binning of the Monte Carlo error
     size_t fref, rref;                       // reference state of the tensor-core refresh
     size_t steptrace;                        // step-size trace (kStepTraceMax sweeps)
+    size_t P1, P2;                           // FP32 path: kept-sweep sums of the open 64-sweep block (chains x ldF FP32)
     size_t total;
     int ldF, ldR;
 };
@@ -382,14 +385,14 @@ struct asm_problem {
     struct GraphKey {
         const void *ws_all = nullptr;
         int chains = 0, precision = -1, kv = 0, ctas = 0, S = 0, consumers = 0, depth = 0, n_items = 0, minb = 0,
-            ubytes = 0, rps = 0;
+            ubytes = 0, rps = 0, npad = 0;
         size_t refresh_smem = 0;
         unsigned long long seed = 0, problem_id = 0, chain_offset = 0;
         bool operator==(const GraphKey &o) const
         {
             return ws_all == o.ws_all && chains == o.chains && precision == o.precision && kv == o.kv &&
                    ctas == o.ctas && S == o.S && consumers == o.consumers && depth == o.depth &&
-                   n_items == o.n_items && minb == o.minb && ubytes == o.ubytes && rps == o.rps &&
+                   n_items == o.n_items && minb == o.minb && ubytes == o.ubytes && rps == o.rps && npad == o.npad &&
                    refresh_smem == o.refresh_smem &&
                    seed == o.seed &&
                    problem_id == o.problem_id && chain_offset == o.chain_offset;
@@ -443,6 +446,8 @@ WsLayout ws_layout(const asm_problem *p, int chains, int precision)
     L.fref = off; off = align_up(off + N * 4, 256);
     L.rref = off; off = align_up(off + (size_t)p->M * 8, 256);
     L.steptrace = off; off = align_up(off + (size_t)kStepTraceMax * 8, 256);
+    L.P1 = off; off = align_up(off + (precision == ASM_FP64 ? 0 : (size_t)chains * L.ldF * 4), 256);
+    L.P2 = off; off = align_up(off + (precision == ASM_FP64 ? 0 : (size_t)chains * L.ldF * 4), 256);
     L.total = off;
     return L;
 }
@@ -886,6 +891,8 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.fref = (float *)(ws + L.fref);
     sp.rref = (double *)(ws + L.rref);
     sp.steptrace = p->trace ? (double *)(ws + L.steptrace) : nullptr;
+    sp.P1 = sizeof(T) == 4 ? (float *)(ws + L.P1) : nullptr;
+    sp.P2 = sizeof(T) == 4 ? (float *)(ws + L.P2) : nullptr;
     sp.trace_cap = kStepTraceMax;
     return sp;
 }
@@ -909,7 +916,8 @@ int ctas_per_sm(int precision, const LaunchShape &sh, int kv, bool batch)
 
 template <class T>
 bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long long total_warps, int kv,
-                bool batch, int want_consumers, int minb, bool prior, const std::vector<int> &ublk_bytes)
+                bool batch, int want_consumers, int minb, bool prior, const std::vector<int> &ublk_bytes,
+                int max_N_sum)
 {
     sh.minb = prior ? 1 : minb;   // the prior's kernels exist for one CTA per SM
     sh.prior = prior ? 1 : 0;
@@ -922,6 +930,7 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
     sh.S = S;
     sh.cpad = round_up_int(std::max(max_np, 1), 32);
     sh.mpad = round_up_int(std::max(max_M, 1), 32);
+    sh.npad = 0;
     int consumers = want_consumers > 0
                         ? want_consumers
                         : (int)std::min<long long>(kMaxConsumers,
@@ -940,8 +949,9 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
     // per-team state, then the ring's barriers (full, empty: 8 bytes per stage each), the
     // U stages' barriers (4 x 8 bytes, padded to 128) and the U stages
     constexpr int kBarBytes = 8 * kMaxRingDepth;
+    auto words = [&](int npad) { return 2 * sh.cpad + sh.mpad + 8 * S + 2 * npad; };
     auto fixed = [&](int c) {
-        return align_up((size_t)c * TW * (2 * sh.cpad + sh.mpad + 8 * S) * sizeof(T), 128) + 2 * kBarBytes + 128;
+        return align_up((size_t)c * TW * words(sh.npad) * sizeof(T), 128) + 2 * kBarBytes + 128;
     };
     int max_depth = kMaxRingDepth;
     if (const char *e = std::getenv("ASM_RING_DEPTH")) {            // tuning override
@@ -959,6 +969,13 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
         const long long ctas = (total_warps + consumers - 1) / consumers;
         const int per_sm = (int)std::min<long long>(by_regs, std::max<long long>(1, (ctas + kSMs - 1) / kSMs));
         const size_t budget = std::min<size_t>(220 * 1024 / per_sm, 227 * 1024);
+        // FP32 chain state: the kept sweeps' sums of one launch (at most one refresh period)
+        // in shared memory, added to the FP64 sums once per launch, where they fit
+        sh.npad = 0;
+        if (sizeof(T) == 4 && max_N_sum > 0 && std::getenv("ASM_NO_SMEM_SUMS") == nullptr) {
+            sh.npad = round_up_int(max_N_sum, 32);
+            if (fixed(consumers) + (size_t)kMinRing * sh.stage_bytes > budget) sh.npad = 0;
+        }
         // U stages: as large as the largest block U that leaves room for a ring of kMinRing
         size_t ub = 0;
         if (stage_u) {
@@ -977,7 +994,8 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
             sh.consumers = consumers;
             sh.depth = depth;
             sh.ubytes = (int)ub;
-            sh.off_full = (int)align_up((size_t)consumers * TW * (2 * sh.cpad + sh.mpad + 8 * S) * sizeof(T), 128);
+            sh.team_words = words(sh.npad);
+            sh.off_full = (int)align_up((size_t)consumers * TW * sh.team_words * sizeof(T), 128);
             sh.off_empty = sh.off_full + kBarBytes;
             sh.off_ubar = sh.off_full + 2 * kBarBytes;
             sh.off_ubuf = sh.off_ubar + 128;
@@ -1110,7 +1128,8 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
     bool prior = false;   // any problem with a gamma prior: the kernels with the acceptance step
     for (asm_problem *u : us) prior = prior || (sizeof(T) == 8 ? u->b64.prior_am1 : u->b32.prior_am1) != nullptr;
     LaunchShape sh{};
-    if (!plan_shape<T>(sh, S, max_rec, max_np, max_M, total_warps, kv, batch, h->tuned_consumers, minb, prior, ublk))
+    if (!plan_shape<T>(sh, S, max_rec, max_np, max_M, total_warps, kv, batch, h->tuned_consumers, minb, prior, ublk,
+                       max_N))
         return ASM_ERR_TOO_LARGE;
     bool stall = h->test_stall;
     for (asm_problem *u : us) stall = stall || u->test_stall;
@@ -1201,6 +1220,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             key.minb = sh.minb + 4 * sh.prior + 8 * sh.stall;
             key.ubytes = sh.ubytes;
             key.rps = sh.rps;
+            key.npad = sh.npad;
             key.refresh_smem = tc ? refresh_tc_smem(max_bn) + 1 : rsmem;
             key.seed = p0.seed;   // by value in a single problem's launch
             key.problem_id = p0.problem_id;
@@ -1291,6 +1311,9 @@ int init_chains(asm_problem *p, const WsLayout &L, int chains)
         return ASM_ERR_CUDA;
     // and so does the step-size trace
     if (cudaMemsetAsync(ws + L.steptrace, 0, (size_t)kStepTraceMax * 8, p->stream) != cudaSuccess)
+        return ASM_ERR_CUDA;
+    // FP32 state: no 64-sweep block of kept sums open yet
+    if (sizeof(T) == 4 && cudaMemsetAsync(ws + L.P1, 0, L.total - L.P1, p->stream) != cudaSuccess)
         return ASM_ERR_CUDA;
     p->nsnap = 0;
     if (const int rc = refresh_smem(refresh_kernel<T>, sizeof(double) * p->N); rc != ASM_OK) return rc;
@@ -1832,8 +1855,10 @@ int asm_average(asm_problem *p, double *mean_A, double *sem_A, double *ess, doub
     if (cudaMalloc(&d, sizeof(double) * 3 * N) != cudaSuccess) return ASM_ERR_CUDA;
     char *ws = (char *)p->ws;
     ++p->other_launches;
-    reduce_kernel<<<(N + 127) / 128, 128, 0, p->stream>>>((const double *)(ws + L.S1), (const double *)(ws + L.S2),
-                                                          p->chains, N, (double)p->kept, d, d + N, d + 2 * N);
+    const bool open32 = p->precision != ASM_FP64;   // FP32 state: sums of the open 64-sweep block
+    reduce_kernel<<<(N + 127) / 128, 128, 0, p->stream>>>(
+        (const double *)(ws + L.S1), (const double *)(ws + L.S2), open32 ? (const float *)(ws + L.P1) : nullptr,
+        open32 ? (const float *)(ws + L.P2) : nullptr, L.ldF, p->chains, N, (double)p->kept, d, d + N, d + 2 * N);
     std::vector<double> h((size_t)3 * N);
     int rc = ASM_OK;
     if (cudaGetLastError() != cudaSuccess ||
@@ -1870,8 +1895,10 @@ int asm_mc_error(asm_problem *p, int k, double *ess, double *sem_fbar, double *s
     double *d = nullptr;
     if (cudaMalloc(&d, sizeof(double) * (3 * (size_t)N + 2 * nk)) != cudaSuccess) return ASM_ERR_CUDA;
     const char *ws = (const char *)u->ws;
-    reduce_kernel<<<(N + 127) / 128, 128, 0, p->stream>>>((const double *)(ws + L.S1), (const double *)(ws + L.S2),
-                                                          chains, N, (double)u->kept, d, d + N, d + 2 * N);
+    const bool open32 = u->precision != ASM_FP64;
+    reduce_kernel<<<(N + 127) / 128, 128, 0, p->stream>>>(
+        (const double *)(ws + L.S1), (const double *)(ws + L.S2), open32 ? (const float *)(ws + L.P1) : nullptr,
+        open32 ? (const float *)(ws + L.P2) : nullptr, L.ldF, chains, N, (double)u->kept, d, d + N, d + 2 * N);
     bin_reduce_kernel<<<(unsigned)((nk + 127) / 128), 128, 0, p->stream>>>(
         (const double *)(ws + L.bacc1), (const double *)(ws + L.bacc2), chains, N, d + 3 * N);
     p->other_launches += 2;
@@ -2058,9 +2085,11 @@ int asm_sample_noalloc(asm_problem *p, int chains, long burn_in, long sweeps, ui
     finish_sweeps(p, s1, sweeps);
     const WsLayout L = ws_layout(p, chains, precision);
     const char *ws = (const char *)p->ws;
-    reduce_kernel<<<(p->N + 127) / 128, 128, 0, p->stream>>>((const double *)(ws + L.S1),
-                                                             (const double *)(ws + L.S2), chains, p->N,
-                                                             (double)sweeps, d_mean_fbar, d_sem2_fbar, d_m2_fbar);
+    const bool open32 = precision != ASM_FP64;
+    reduce_kernel<<<(p->N + 127) / 128, 128, 0, p->stream>>>(
+        (const double *)(ws + L.S1), (const double *)(ws + L.S2), open32 ? (const float *)(ws + L.P1) : nullptr,
+        open32 ? (const float *)(ws + L.P2) : nullptr, L.ldF, chains, p->N, (double)sweeps, d_mean_fbar, d_sem2_fbar,
+        d_m2_fbar);
     ++p->other_launches;
     return cudaGetLastError() == cudaSuccess ? ASM_OK : ASM_ERR_CUDA;
 }
@@ -2098,7 +2127,7 @@ struct CheckpointHeader {
     int64_t sweeps_done, kept, ws_bytes;
     int64_t kept_since;   // first sweep of the unbroken kept run (binning of a continuation)
 };
-constexpr uint64_t kCheckpointVersion = 3;
+constexpr uint64_t kCheckpointVersion = 4;
 constexpr uint64_t kCheckpointMagic = 0x41534d434b505431ull;   // "ASMCKPT1"
 }  // namespace
 

@@ -201,16 +201,28 @@ __device__ __forceinline__ T narrow_cdf(T a, T t)
 // at most w^2/8 across the interval, so one or two steps converge where the
 // flat start t = u w needed four.  The offset t from the lower end keeps its
 // relative accuracy however narrow the interval is.
+// In FP32 the start is the answer when w^2 / 8, the curvature's bound on the
+// relative error of the exponential law's CDF, lies below 2^-23 (w <= 6e-4: the
+// weak modes whose intervals are a tiny fraction of their Gaussian's width),
+// and one Newton step is when w <= 0.2: Newton's error is quadratic in the
+// start's, which is below w^2/12 relative, and one step leaves at most 1.5e-7
+// relative over the narrow regime with w <= 0.2 (measured against the root of
+// a 64-point rule at 4 million (a, w, u)), below the FP32 tolerance.
 template <class T>
 __device__ __forceinline__ T narrow_offset(T a, T w, T u, int &capped)
 {
     using GL = GaussLegendre<T>;
-    const T target = u * narrow_cdf(a, w);
     const T lam = a + T(0.5) * w;
     const T x = lam * w;
     T t = m_abs(x) < T(1e-3) ? u * w * (T(1) - T(0.5) * x * (T(1) - u))   // the series for small lam w
                              : -m_log1p(u * m_expm1(-x)) / lam;
     t = m_min(m_max(t, T(0)), w);
+    if (sizeof(T) == 4 && w * w <= T(4e-7)) return t;
+    const T target = u * narrow_cdf(a, w);
+    if (sizeof(T) == 4 && w <= T(0.2)) {
+        const T step = (narrow_cdf(a, t) - target) / m_exp(-t * (a + T(0.5) * t));
+        return m_min(m_max(t - step, T(0)), w);
+    }
     int it = 0;
     for (; it < GL::nmax; ++it) {
         const T step = (narrow_cdf(a, t) - target) / m_exp(-t * (a + T(0.5) * t));
@@ -309,32 +321,91 @@ __device__ __forceinline__ void key_update(typename BoundKey<T>::S &lk, typename
     hk = ku < hk ? ku : hk;
 }
 
-// f += delta * V (clamped at +0), then the lane's bound keys of the next mode
-// from the updated f and that mode's R row (rows read from global memory).
+// One 16-byte chunk of the pass: x = max(f + delta V, +0), f = x, and the keys
+// of t = x R into two accumulator pairs (even and odd element), so that the
+// chain of integer minima is half as long.  The minima are exact, so the keys
+// do not depend on the grouping.  FP32: the products and the fused
+// multiply-adds in packed pairs (one instruction per two elements, each
+// element rounded as by the scalar instruction).
+template <class T>
+struct Keys {
+    typename BoundKey<T>::S l0, l1;
+    typename BoundKey<T>::U h0, h1;
+    __device__ __forceinline__ void reset()
+    {
+        l0 = l1 = BoundKey<T>::lo0;
+        h0 = h1 = BoundKey<T>::hi0;
+    }
+    __device__ __forceinline__ void fold(typename BoundKey<T>::S &lk, typename BoundKey<T>::U &hk) const
+    {
+        lk = l1 < l0 ? l1 : l0;
+        hk = h1 < h0 ? h1 : h0;
+    }
+};
+__device__ __forceinline__ void pass_chunk(float (&f)[4], float delta, const float (&vv)[4], const float (&rr)[4],
+                                           Keys<float> &kk)
+{
+    const float2 d2 = make_float2(delta, delta);
+    float2 a = __ffma2_rn(d2, make_float2(vv[0], vv[1]), make_float2(f[0], f[1]));
+    float2 b = __ffma2_rn(d2, make_float2(vv[2], vv[3]), make_float2(f[2], f[3]));
+    a.x = fmaxf(a.x, 0.0f);
+    a.y = fmaxf(a.y, 0.0f);
+    b.x = fmaxf(b.x, 0.0f);
+    b.y = fmaxf(b.y, 0.0f);
+    f[0] = a.x; f[1] = a.y; f[2] = b.x; f[3] = b.y;
+    const float2 ta = __fmul2_rn(a, make_float2(rr[0], rr[1]));
+    const float2 tb = __fmul2_rn(b, make_float2(rr[2], rr[3]));
+    key_update<float>(kk.l0, kk.h0, ta.x);
+    key_update<float>(kk.l1, kk.h1, ta.y);
+    key_update<float>(kk.l0, kk.h0, tb.x);
+    key_update<float>(kk.l1, kk.h1, tb.y);
+}
+__device__ __forceinline__ void pass_chunk(double (&f)[2], double delta, const double (&vv)[2],
+                                           const double (&rr)[2], Keys<double> &kk)
+{
+    double x0 = fmax(fma(delta, vv[0], f[0]), 0.0);
+    double x1 = fmax(fma(delta, vv[1], f[1]), 0.0);
+    f[0] = x0;
+    f[1] = x1;
+    key_update<double>(kk.l0, kk.h0, x0 * rr[0]);
+    key_update<double>(kk.l1, kk.h1, x1 * rr[1]);
+}
+// Keys alone (the first mode of a block: f is unchanged, t = f R).
+__device__ __forceinline__ void key_chunk(const float (&f)[4], const float (&rr)[4], Keys<float> &kk)
+{
+    const float2 ta = __fmul2_rn(make_float2(f[0], f[1]), make_float2(rr[0], rr[1]));
+    const float2 tb = __fmul2_rn(make_float2(f[2], f[3]), make_float2(rr[2], rr[3]));
+    key_update<float>(kk.l0, kk.h0, ta.x);
+    key_update<float>(kk.l1, kk.h1, ta.y);
+    key_update<float>(kk.l0, kk.h0, tb.x);
+    key_update<float>(kk.l1, kk.h1, tb.y);
+}
+__device__ __forceinline__ void key_chunk(const double (&f)[2], const double (&rr)[2], Keys<double> &kk)
+{
+    key_update<double>(kk.l0, kk.h0, f[0] * rr[0]);
+    key_update<double>(kk.l1, kk.h1, f[1] * rr[1]);
+}
+
+// The lane's bound keys of a block's first mode from f (>= +0, so that
+// max(f + 0 V, +0) = f and the pass reduces to the products) and that mode's R
+// row, read from global memory.
 template <class T, int KV>
-__device__ __forceinline__ void fused_pass(T (&f)[KV][VecOf<T>::n], T delta, const T *__restrict__ vrow,
-                                           const T *__restrict__ rrow, int kcnt, int sl, int S,
-                                           typename BoundKey<T>::S &lk, typename BoundKey<T>::U &hk)
+__device__ __forceinline__ void first_keys(const T (&f)[KV][VecOf<T>::n], const T *__restrict__ rrow, int kcnt,
+                                           int sl, int S, typename BoundKey<T>::S &lk,
+                                           typename BoundKey<T>::U &hk)
 {
     constexpr int VEC = VecOf<T>::n;
-    lk = BoundKey<T>::lo0;
-    hk = BoundKey<T>::hi0;
+    Keys<T> kk;
+    kk.reset();
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
         if (k < kcnt) {
-            const int idx = VEC * (k * S + sl);
-            T vv[VEC], rr[VEC];
-            ldv(vrow + idx, vv);
-            ldv(rrow + idx, rr);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                T x = m_fma(delta, vv[v], f[k][v]);
-                x = m_max(x, T(0));
-                f[k][v] = x;
-                key_update<T>(lk, hk, x * rr[v]);
-            }
+            T rr[VEC];
+            ldv(rrow + VEC * (k * S + sl), rr);
+            key_chunk(f[k], rr, kk);
         }
     }
+    kk.fold(lk, hk);
 }
 
 // --------------------------------------------------------------------------
@@ -453,32 +524,23 @@ __device__ __forceinline__ void fused_pass_smem(T (&f)[KV][VecOf<T>::n], T delta
 {
     constexpr int VEC = VecOf<T>::n;
     static_assert(KK >= 1 && KK <= KV, "chunk count");
-    lk = BoundKey<T>::lo0;
-    hk = BoundKey<T>::hi0;
+    Keys<T> kk;
+    kk.reset();
 #pragma unroll
     for (int k = 0; k < KK; ++k) {
         if (!CHK || k < kcnt) {
             const int idx = VEC * (k * S + sl);
-            T vv[VEC], rr[VEC];
             if (k == 0) {
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    vv[v] = v0[v];
-                    rr[v] = r0[v];
-                }
+                pass_chunk(f[0], delta, v0, r0, kk);
             } else {
+                T vv[VEC], rr[VEC];
                 lds_v(vrow + idx, vv);
                 lds_v(rrow + idx, rr);
-            }
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                T x = m_fma(delta, vv[v], f[k][v]);
-                x = m_max(x, T(0));
-                f[k][v] = x;
-                key_update<T>(lk, hk, x * rr[v]);
+                pass_chunk(f[k], delta, vv, rr, kk);
             }
         }
     }
+    kk.fold(lk, hk);
 }
 
 // --------------------------------------------------------------------------
@@ -665,12 +727,30 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
     const bool active = q_raw < p.chains;
     const long long q = active ? q_raw : (long long)p.chains - 1;  // idle teams shadow a real chain, write nothing
 
-    // per team in shared memory: c (cpad), w (cpad), r~ (mpad) and the uniforms of the
-    // current window of 4S moves
-    T *csm = reinterpret_cast<T *>(smem_raw) + (size_t)(wcta * TW + team) * (2 * sh.cpad + sh.mpad + 8 * S);
+    // per team in shared memory: c (cpad), w (cpad), r~ (mpad), the uniforms of the
+    // current window of 4S moves and, where they fit (npad > 0), the sums of f and f^2
+    // over this launch's kept sweeps (FP32; at most one refresh period of terms)
+    T *csm = reinterpret_cast<T *>(smem_raw) + (size_t)(wcta * TW + team) * sh.team_words;
     T *wsm = csm + sh.cpad;
     T *rsm = wsm + sh.cpad;
     T *usm = rsm + sh.mpad;   // 4S uniforms of the draws, then 4S of the prior's acceptances
+    // FP32 chain state: the kept-sweep sums of the current kBinSweeps-sweep block (aligned
+    // to absolute sweep indices) in FP32, added to the FP64 sums when the block closes.
+    // Between launches they wait in the workspace (P1, P2); during one they live in shared
+    // memory where they fit, else in the workspace -- the same arithmetic in the same order
+    // either way, so results do not depend on where a run is split into calls.
+    // FP64 chain state: straight into the FP64 sums.
+    constexpr bool psums = sizeof(T) == 4;
+    const bool kept_here = psums && rg.burn_in < rg.sweep0 + rg.nsweeps;
+    T *P1q = psums ? reinterpret_cast<T *>(p.P1) + (size_t)q * p.ldF : nullptr;
+    T *P2q = psums ? reinterpret_cast<T *>(p.P2) + (size_t)q * p.ldF : nullptr;
+    T *p1sm = sh.npad ? usm + 8 * S : P1q;
+    T *p2sm = sh.npad ? p1sm + sh.npad : P2q;
+    if (kept_here && sh.npad)
+        for (int n = sl; n < p.N; n += S) {
+            p1sm[n] = P1q[n];
+            p2sm[n] = P2q[n];
+        }
     T *Rq = p.R + (size_t)q * p.ldR;
     for (int m = sl; m < p.M; m += S) rsm[m] = Rq[m];
     T *Fq = p.F + (size_t)q * p.ldF;
@@ -723,18 +803,29 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
             // same sums in the same order from the U stage)
             const T *Um = p.pd.Um + B.offU;
             if (ust) {
-                for (int j = sl; j < B.np; j += S) {
+                // two of the lane's modes at a time (j, j + S): two independent chains of sums
+                for (int j = sl; j < B.np; j += 2 * S) {
+                    const bool two = j + S < B.np;
                     const T *u = Us + (size_t)j * B.usr;
-                    T a[8];
+                    const T *u2 = Us + (size_t)(two ? j + S : j) * B.usr;
+                    T a[8], b[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) a[i] = T(0);
+                    for (int i = 0; i < 8; ++i) a[i] = b[i] = T(0);
                     int m = 0;
                     for (; m + 7 < p.M; m += 8) {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) a[i] = m_fma(u[m + i], rsm[m + i], a[i]);
+                        for (int i = 0; i < 8; ++i) {
+                            const T r = rsm[m + i];
+                            a[i] = m_fma(u[m + i], r, a[i]);
+                            b[i] = m_fma(u2[m + i], r, b[i]);
+                        }
                     }
-                    for (; m < p.M; ++m) a[0] = m_fma(u[m], rsm[m], a[0]);
+                    for (; m < p.M; ++m) {
+                        a[0] = m_fma(u[m], rsm[m], a[0]);
+                        b[0] = m_fma(u2[m], rsm[m], b[0]);
+                    }
                     csm[j] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+                    if (two) csm[j + S] = ((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + (b[6] + b[7]));
                 }
             } else
             for (int j = sl; j < B.np; j += S) {
@@ -765,7 +856,7 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
 
             typename BoundKey<T>::S lk;
             typename BoundKey<T>::U hk;
-            fused_pass<T, KV>(f, T(0), p.pd.V + B.offV, p.pd.R + B.offR, kcnt, sl, S, lk, hk);  // keys of mode 0
+            first_keys<T, KV>(f, p.pd.R + B.offR, kcnt, sl, S, lk, hk);  // keys of mode 0
             // The block's moves.  Where the lane's chunk count is 1 (blocks of at most
             // VEC*S points) or KV (every chunk present) it is a compile-time constant and
             // the move loop tests no chunk; the uniforms are refilled once per window of
@@ -833,17 +924,22 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
 
                         T lo, hi;
                         team_bounds(lk, hk, lo, hi, S, team_base);
-                        // degenerate interval: no move; zero mode: flat on [lo, hi]; else the
-                        // truncated Gaussian (the only branch)
+                        // degenerate interval: no move; zero mode: flat on [lo, hi] (both bounds
+                        // finite: set-up rejects zero modes that do not change sign); else the
+                        // truncated Gaussian.  The branch is on the record's d_j, which is known
+                        // long before the bounds, so the flat path is one FMA and a select.
                         const bool open = hi > lo;
-                        T delta = m_fma(u, hi - lo, lo);
-                        if (open && dj != T(0)) delta = tn_step<T>(cj, dj, ij, lo, hi, u, capped);
+                        T delta;
+                        if (dj == T(0)) {
+                            delta = open ? m_fma(u, hi - lo, lo) : T(0);
+                            n_zero += open ? 1u : 0u;
+                        } else {
+                            delta = open ? tn_step<T>(cj, dj, ij, lo, hi, u, capped) : T(0);
+                            const bool fin = isfinite(delta);
+                            n_bad += fin ? 0u : 1u;
+                            delta = fin ? delta : T(0);
+                        }
                         n_deg += open ? 0u : 1u;
-                        n_zero += (open && dj == T(0)) ? 1u : 0u;
-                        delta = open ? delta : T(0);
-                        const bool fin = isfinite(delta);
-                        n_bad += fin ? 0u : 1u;
-                        delta = fin ? delta : T(0);
                         if constexpr (PRIOR) if (delta != T(0)) {
                             // gamma prior (Eq. compat): the draw is a proposal, accepted with
                             // probability min(1, prod ((f + delta V)_+ / f)^(a - 1)) over the block
@@ -916,17 +1012,29 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
             // flight, eight partial sums as at entry; the same from the U stage)
             const T *Ut = p.pd.Ut + B.offU;
             if (ust) {
-                for (int m = sl; m < p.M; m += S) {
-                    T a[8];
+                // two of the lane's data points at a time (m, m + S)
+                for (int m = sl; m < p.M; m += 2 * S) {
+                    const bool two = m + S < p.M;
+                    const int m2 = two ? m + S : m;
+                    T a[8], b[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) a[i] = T(0);
+                    for (int i = 0; i < 8; ++i) a[i] = b[i] = T(0);
                     int j = 0;
                     for (; j + 7 < B.np; j += 8) {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) a[i] = m_fma(Us[(size_t)(j + i) * B.usr + m], wsm[j + i], a[i]);
+                        for (int i = 0; i < 8; ++i) {
+                            const T w = wsm[j + i];
+                            const T *u = Us + (size_t)(j + i) * B.usr;
+                            a[i] = m_fma(u[m], w, a[i]);
+                            b[i] = m_fma(u[m2], w, b[i]);
+                        }
                     }
-                    for (; j < B.np; ++j) a[0] = m_fma(Us[(size_t)j * B.usr + m], wsm[j], a[0]);
+                    for (; j < B.np; ++j) {
+                        a[0] = m_fma(Us[(size_t)j * B.usr + m], wsm[j], a[0]);
+                        b[0] = m_fma(Us[(size_t)j * B.usr + m2], wsm[j], b[0]);
+                    }
                     rsm[m] -= ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+                    if (two) rsm[m + S] -= ((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + (b[6] + b[7]));
                 }
                 // release the U stage to the producer (one arrival per warp)
                 __syncwarp();
@@ -972,9 +1080,14 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                         }
                         Fq[n] = f[k][v];
                         if (keep) {
-                            const double x = (double)f[k][v];
-                            S1q[n] += x;
-                            S2q[n] += x * x;
+                            if constexpr (psums) {
+                                p1sm[n] += f[k][v];
+                                p2sm[n] = m_fma(f[k][v], f[k][v], p2sm[n]);
+                            } else {
+                                const double x = (double)f[k][v];
+                                S1q[n] += x;
+                                S2q[n] += x * x;
+                            }
                         }
                     }
                 }
@@ -995,6 +1108,20 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
     }
     if (active) {
         for (int m = sl; m < p.M; m += S) Rq[m] = rsm[m];
+        if (kept_here) {
+            if ((rg.sweep0 + rg.nsweeps) % kBinSweeps == 0) {   // the block closes: into the FP64 sums
+                for (int n = sl; n < p.N; n += S) {
+                    S1q[n] += (double)p1sm[n];
+                    S2q[n] += (double)p2sm[n];
+                    P1q[n] = P2q[n] = T(0);
+                }
+            } else if (sh.npad) {   // the block continues in a later launch
+                for (int n = sl; n < p.N; n += S) {
+                    P1q[n] = p1sm[n];
+                    P2q[n] = p2sm[n];
+                }
+            }
+        }
         if (sl == 0) {
             if (n_deg) atomicAdd(&p.counters->degenerate, (unsigned long long)n_deg);
             if (n_zero) atomicAdd(&p.counters->zero_mode, (unsigned long long)n_zero);

@@ -5,9 +5,12 @@ FP64 oracle at N_omega = 250 on the uniform and the Gaussian-density grid.
 
 Both runs share the level schedule (same seed, problem id 0) on disjoint chain
 ids; <fbar> must agree within 4 combined standard errors at every grid point
-(1024 GPU and 128 oracle chains, so that the spread of the chain means
-estimates each standard error to a few per cent).
-The relative L2 error of <A> is checked against the same combined error.
+(the library's binned error, asm_mc_error, and the spread of 128 independent
+oracle chain means, so that each standard error is itself estimated to a few
+per cent).  The relative L2 error of <A> is checked against the same combined
+error.  The largest grid, N_omega = 2000, is compared the same way, with the
+distribution of the z-scores checked as well (mean square near 1, no more
+than 1 % beyond 3).
 """
 import numpy as np
 import pytest
@@ -30,22 +33,43 @@ def _cuda():
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("density", ["uniform", "gaussian"])
-def test_grid_sweep_mixed_against_oracle(density):
-    p = W.grid_sweep_problem(250, density, chains=1024)
-    # enough chains on both sides that the standard errors themselves are well estimated
-    chains_gpu, chains_cpu, burn, sweeps, seed = 1024, 128, 200, 1000, 55
-    gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w)
+def _compare(n_omega, density, chains_gpu, chains_cpu, burn, sweeps, seed, oracle_factors=False):
+    p = W.grid_sweep_problem(n_omega, density, chains=chains_gpu)
+    op = O.OracleProblem(p.K, p.G, p.C, p.levels)
+    gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w, factors=op.decomposition() if oracle_factors else None)
     gp.sample(chains_gpu, burn, sweeps, seed, precision=asm.ASM_MIXED)
     st = gp.status()
     assert st["tc_refreshes"] >= (burn + sweeps) // 64 and st["timeouts"] == 0 and st["nonfinite_moves"] == 0
     sg = gp.average()
-    op = O.OracleProblem(p.K, p.G, p.C, p.levels)
+    sem_gpu = gp.mc_error()["sem_fbar"]
     r = op.run(chains_cpu, burn, sweeps, seed=seed, threads=0, chain_offset=chains_gpu)
     so = O.summarize(r["S1"], r["S2"], sweeps, p.w)
-    se = np.hypot(sg["sem_fbar"], so["sem_fbar"])
+    se = np.hypot(sem_gpu, so["sem_fbar"])
     z = np.abs(sg["mean_fbar"] - so["mean_fbar"]) / se
-    assert np.max(z) < Z_MAX, float(np.max(z))
     l2 = np.linalg.norm(sg["mean_A"] - so["mean_A"]) / np.linalg.norm(so["mean_A"])
     l2_se = np.linalg.norm(se / p.w) / np.linalg.norm(so["mean_A"])
+    return z, l2, l2_se
+
+
+@pytest.mark.parametrize("density", ["uniform", "gaussian"])
+def test_grid_sweep_mixed_against_oracle(density):
+    # enough chains on both sides that the standard errors themselves are well estimated
+    z, l2, l2_se = _compare(250, density, 1024, 128, 200, 1000, 55)
+    assert np.max(z) < Z_MAX, float(np.max(z))
+    assert l2 < 3.0 * l2_se, (l2, l2_se)
+
+
+def test_grid_sweep_largest_grid_against_oracle():
+    """N_omega = 2000 (the largest grid of the sweep): 1024 GPU chains against
+    128 oracle chains, 200 burn-in + 300 kept sweeps each, the library given
+    the oracle's factors.  At this size 200 sweeps do not reach equilibrium:
+    runs in two mode bases (the library's SVD and the oracle's) are two Markov
+    chains with the same stationary law but different transients, which the
+    standard errors do not measure (oracle against oracle with different level
+    schedules differs by tens of standard errors here); in the oracle's basis
+    and on its level schedule both sides run the same chain."""
+    z, l2, l2_se = _compare(2000, "uniform", 1024, 128, 200, 300, 56, oracle_factors=True)
+    assert np.max(z) < Z_MAX, float(np.max(z))
+    assert 0.75 < np.mean(z ** 2) < 1.33, float(np.mean(z ** 2))
+    assert np.mean(z > 3.0) <= 0.01, float(np.mean(z > 3.0))
     assert l2 < 3.0 * l2_se, (l2, l2_se)
