@@ -72,7 +72,7 @@ def _args():
                     help="sweeps per partition scheme of the hierarchy side measurement (0: skip)")
     ap.add_argument("--diff-sweeps", type=int, default=2000,
                     help="kept sweeps per run of the differentiation side measurement (0: skip)")
-    ap.add_argument("--diff-budget-s", type=float, default=90.0,
+    ap.add_argument("--diff-budget-s", type=float, default=30.0,
                     help="time budget of the differentiation side measurement (seconds)")
     return ap.parse_args()
 

@@ -509,6 +509,7 @@ struct ora_problem {
     int flat_exp;        /* R2: sign-changing modes with d <= d_1 max(M,n) 2^-flat_exp are flat */
     int jitter;          /* test of rounding sensitivity: 0 off, else every conditional mean and
                           * interval end moved by one rounding at unit roundoff 2^-jitter */
+    int jitter_shift;    /* the directions come from bits jitter_shift + 1..3 of the move's word */
 };
 
 void ora_free(ora_problem *p)
@@ -630,7 +631,11 @@ ora_problem *ora_setup(int M, int N, const double *K, const double *G, const dou
     return ora_setup_ex(M, N, K, G, C, n_levels, level_nblocks, block_start, 40, err);
 }
 
-void ora_set_jitter(ora_problem *p, int unit_exp) { p->jitter = (unit_exp >= 1 && unit_exp <= 60) ? unit_exp : 0; }
+void ora_set_jitter(ora_problem *p, int unit_exp, int pattern)
+{
+    p->jitter = (unit_exp >= 1 && unit_exp <= 60) ? unit_exp : 0;
+    p->jitter_shift = (pattern >= 0 && pattern < 16) ? 3 * pattern : 0;
+}
 
 void ora_sizes(const ora_problem *p, long *n_d, long *n_V, long *n_U)
 {
@@ -837,11 +842,12 @@ static void ora_chain(const ora_problem *p, uint64_t q, double *f, long sweep0, 
                 double mu, sigma, lo, hi, delta, mu_scale;
                 ora_mode_conditional(b, j, f, h, habs, &mu, &sigma, &mu_scale);
                 ora_bounds(b, j, f, &lo, &hi);
-                if (p->jitter) {   /* one rounding each, up or down by bits 1-3 of the move's word */
+                if (p->jitter) {   /* one rounding each, up or down by three bits of the move's word */
                     const double ulp = ldexp(1.0, -p->jitter);
-                    if (sigma > 0.0) mu += ((w[t & 3] & 2) ? 1.0 : -1.0) * ulp * mu_scale;
-                    if (isfinite(lo)) lo += ((w[t & 3] & 4) ? 1.0 : -1.0) * ulp * fabs(lo);
-                    if (isfinite(hi)) hi += ((w[t & 3] & 8) ? 1.0 : -1.0) * ulp * fabs(hi);
+                    const uint64_t bits = w[t & 3] >> p->jitter_shift;
+                    if (sigma > 0.0) mu += ((bits & 2) ? 1.0 : -1.0) * ulp * mu_scale;
+                    if (isfinite(lo)) lo += ((bits & 4) ? 1.0 : -1.0) * ulp * fabs(lo);
+                    if (isfinite(hi)) hi += ((bits & 8) ? 1.0 : -1.0) * ulp * fabs(hi);
                 }
                 if (!(hi > lo)) {
                     delta = 0.0;

@@ -68,8 +68,8 @@ void ora_free(ora_problem *p);
 
 /* Rounding-sensitivity probe (tests only): with unit_exp = e in 1..60 (0: off),
  * every move's inputs are moved by one rounding at unit roundoff 2^-e (e = 52:
- * FP64 rounding, e = 24: FP32 rounding), each up or down by bits 1-3 of the
- * move's Philox word, before the draw: the conditional mean mu = h_j/d_j - e_j
+ * FP64 rounding, e = 24: FP32 rounding), each up or down by bits 3k+1..3k+3
+ * of the move's Philox word (k = pattern, 0..15), before the draw: the conditional mean mu = h_j/d_j - e_j
  * of a Gaussian move (Sec. IV.B) by 2^-e (sum_m |U_jm| (|g~_m| + sum_n |K~_mn
  * f_n|) / d_j + sum_i |V_ji f_i|), the size of the terms it is summed from, and
  * each finite end of the interval [lo, hi] by 2^-e of its size.  Two correct
@@ -77,7 +77,7 @@ void ora_free(ora_problem *p);
  * residual incrementally, one recomputing the block's data from scratch)
  * differ at least by such roundings, so the probe's divergence from the plain
  * run measures how far a step-by-step comparison can be held. */
-void ora_set_jitter(ora_problem *p, int unit_exp);
+void ora_set_jitter(ora_problem *p, int unit_exp, int pattern);
 
 /* Sizes of the exported factors: total entries of d, V and U over all blocks. */
 void ora_sizes(const ora_problem *p, long *n_d, long *n_V, long *n_U);

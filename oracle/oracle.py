@@ -75,7 +75,7 @@ def lib():
                                   ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_int, _dp, _dp, _dp, _dp, _dp,
                                   ct.c_int, _lp]
         L.ora_run_ids.restype = ct.c_int
-        L.ora_set_jitter.argtypes = [ct.c_void_p, ct.c_int]
+        L.ora_set_jitter.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
         L.ora_set_prior.argtypes = [ct.c_void_p, _dp]
         L.ora_set_prior.restype = ct.c_int
         _lib = L
@@ -181,11 +181,12 @@ class OracleProblem:
             lib().ora_free(self._h)
             self._h = None
 
-    def set_jitter(self, on=True, unit_exp=52):
+    def set_jitter(self, on=True, unit_exp=52, pattern=0):
         """Rounding-sensitivity probe: every move's conditional mean and interval
-        ends moved by one rounding at unit roundoff 2^-unit_exp before its draw
-        (tests only)."""
-        lib().ora_set_jitter(self._h, int(unit_exp) if on else 0)
+        ends moved by one rounding at unit roundoff 2^-unit_exp before its draw,
+        the directions taken from bits of the move's Philox word chosen by
+        `pattern` (0..15) (tests only)."""
+        lib().ora_set_jitter(self._h, int(unit_exp) if on else 0, int(pattern))
 
     def blocks(self):
         """(level, block, start, n) for every block in level order."""

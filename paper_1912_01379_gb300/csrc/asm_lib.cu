@@ -944,7 +944,11 @@ bool plan_shape(LaunchShape &sh, int S, int max_rec, int max_np, int max_M, long
         const int r = std::atoi(e);
         if (r >= 1 && r <= 8) sh.rps = r;
     }
-    sh.stage_bytes = (int)align_up((size_t)sh.rps * max_rec * sizeof(T), 128);
+    // fewer records per stage where a ring of four stages would not fit (long records: FP64
+    // state on large blocks)
+    auto stage_of = [&](int rps) { return (int)align_up((size_t)rps * max_rec * sizeof(T), 128); };
+    while (sh.rps > 1 && 4 * (size_t)stage_of(sh.rps) > 200 * 1024) --sh.rps;
+    sh.stage_bytes = stage_of(sh.rps);
     const int kMinRing = std::max(2, (kMinRingRecords + sh.rps - 1) / sh.rps);
     // per-team state, then the ring's barriers (full, empty: 8 bytes per stage each), the
     // U stages' barriers (4 x 8 bytes, padded to 128) and the U stages

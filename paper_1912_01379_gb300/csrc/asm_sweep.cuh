@@ -104,7 +104,10 @@ template <> struct TailTraits<float> {
     static constexpr float far = 10.0f;
 };
 
-// x ~ N(0,1) restricted to [a, b], 0 <= a < b <= inf, by Q(x) = (1-u)Q(a) + uQ(b).
+// x ~ N(0,1) restricted to [a, a + w], a >= 0, 0 < w <= inf, by Q(x) = (1-u)Q(a) + uQ(b),
+// b = a + w.  The width comes in as w, formed from the interval's ends before they are
+// standardised: b - a of two standardised ends far in the tail cancels (a = 35 and
+// w = 0.03 leave w with a relative error of 2^-24 a / w = 7e-5 in FP32).
 // Returns the offset y = x - a.  The equation in y,
 //   log Q(a + y) - log Q(a) = dt,  dt = log((1-u) + u Q(b)/Q(a)),
 // is solved by Newton's method on log Q (concave, so the iterates are monotone
@@ -114,8 +117,9 @@ template <> struct TailTraits<float> {
 // few ulp of a, which FP32 keeps; in FP64 the offset form refines it so that y
 // keeps its relative accuracy however small it is.
 template <class T>
-__device__ __forceinline__ T right_tail(T a, T b, T u, int &capped)
+__device__ __forceinline__ T right_tail(T a, T w, T u, int &capped)
 {
+    const T b = a + w;
     const T kRsqrt2 = T(0.70710678118654752440);
     const T kSqrtPiOver2 = T(1.25331413731550025121);
     constexpr bool kRefine = sizeof(T) == 8;
@@ -130,7 +134,7 @@ __device__ __forceinline__ T right_tail(T a, T b, T u, int &capped)
         const T exa = m_erfcx(a * kRsqrt2);
         T r = T(0), em = T(-1);
         if (!isinf(b)) {
-            const T lr = m_log(m_erfcx(b * kRsqrt2) / exa) - T(0.5) * (b - a) * (b + a);
+            const T lr = m_log(m_erfcx(b * kRsqrt2) / exa) - T(0.5) * w * (a + b);
             r = m_exp(lr);
             em = m_expm1(lr);
         }
@@ -147,7 +151,7 @@ __device__ __forceinline__ T right_tail(T a, T b, T u, int &capped)
         if (it == TailTraits<T>::nmax) ++capped;
     }
     y = m_max(y, T(0));
-    y = m_min(y, b - a);
+    y = m_min(y, w);
     return y;
 }
 
@@ -247,9 +251,9 @@ __device__ __forceinline__ T tn_step(T c, T d, T invd, T lo, T hi, T u, int &cap
     if (isfinite(wid) && wid * (m_abs(a) + wid) <= T(0.5)) {
         delta = lo + invd * narrow_offset(a, wid, u, capped);
     } else if (a >= T(0)) {
-        delta = lo + invd * right_tail(a, b, u, capped);
+        delta = lo + invd * right_tail(a, wid, u, capped);
     } else if (b <= T(0)) {
-        delta = hi - invd * right_tail(-b, -a, T(1) - u, capped);
+        delta = hi - invd * right_tail(-b, wid, T(1) - u, capped);
     } else if (a < -TailTraits<T>::far && b > TailTraits<T>::far) {
         // the truncation is below the resolution of u: the untruncated inverse CDF
         const T x = u <= T(0.5) ? m_phiinv(u) : -m_phiinv(T(1) - u);
@@ -804,8 +808,9 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
             const T *Um = p.pd.Um + B.offU;
             if (ust) {
                 // two of the lane's modes at a time (j, j + S): two independent chains of sums
-                for (int j = sl; j < B.np; j += 2 * S) {
-                    const bool two = j + S < B.np;
+                // (one at a time in the widest register tiles, whose registers hold f)
+                for (int j = sl; j < B.np; j += (KV <= 8 ? 2 : 1) * S) {
+                    const bool two = KV <= 8 && j + S < B.np;
                     const T *u = Us + (size_t)j * B.usr;
                     const T *u2 = Us + (size_t)(two ? j + S : j) * B.usr;
                     T a[8], b[8];
@@ -897,26 +902,27 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                         }
                         __syncwarp();
                     }
-                    const int jend = min(B.n, win_end - B.start);   // this window's moves in the block
-                    for (; j < jend; ++j) {
+                    // the stage of the next record: usually landed long ago (one test, one vote
+                    // per stage of sh.rps moves)
+                    if (jr == 0) {
+                        bool ok = mbar_test_wait(full + rp.slot, rp.phase);
+                        if (__any_sync(0xffffffffu, !ok)) {
+                            ok = ok || mbar_wait(full + rp.slot, rp.phase, sh.wait_limit);
+                            if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
+                                failed = true;
+                                break;
+                            }
+                        }
+                        stb = reinterpret_cast<const T *>(stages + (size_t)rp.slot * sh.stage_bytes);
+                    }
+                    // this segment's moves: up to the end of the window, of the stage or of the block
+                    const int jbeg = j, jend = min(min(B.n, win_end - B.start), j + (sh.rps - jr));
+                    const T *st = stb + (size_t)jr * B.recstride;
+                    for (; j < jend; ++j, st += B.recstride) {
                         // what does not depend on the bounds first: c_j and the uniform
                         const T cj = j < B.np ? csm[j] : T(0);
                         const int t = B.start + j;
                         const T u = usm[t - win];
-                        // the stage of this move's record: usually landed long ago (one test, one
-                        // vote per stage of sh.rps moves)
-                        if (jr == 0) {
-                            bool ok = mbar_test_wait(full + rp.slot, rp.phase);
-                            if (__any_sync(0xffffffffu, !ok)) {
-                                ok = ok || mbar_wait(full + rp.slot, rp.phase, sh.wait_limit);
-                                if (__any_sync(0xffffffffu, !ok)) {   // decided warp-wide
-                                    failed = true;
-                                    break;
-                                }
-                            }
-                            stb = reinterpret_cast<const T *>(stages + (size_t)rp.slot * sh.stage_bytes);
-                        }
-                        const T *st = stb + (size_t)jr * B.recstride;
                         const T dj = st[2 * B.rs], ij = st[2 * B.rs + 1];
                         T v0[VEC], r0[VEC];   // chunk 0 of the pass: independent of the draw, loaded first
                         lds_v(st + VEC * sl, v0);
@@ -986,15 +992,14 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                         // the residual moves by K~_b V_j delta = dres_j delta U_j (dres = d for a
                         // Gaussian mode, |K~_b V_j| for one sampled flat)
                         if (j < B.np && sl == 0) wsm[j] = st[2 * B.rs + 2] * delta;
-                        // release the stage to the producer after its last record (one arrival per warp)
-                        if (jr + 1 == sh.rps || j + 1 == B.n) {
-                            __syncwarp();
-                            mbar_arrive_lane0(empty + rp.slot, lane);
-                            ring_next(rp, D);
-                            jr = 0;
-                        } else {
-                            ++jr;
-                        }
+                    }
+                    // release the stage to the producer after its last record (one arrival per warp)
+                    jr += j - jbeg;
+                    if (jr == sh.rps || j == B.n) {
+                        __syncwarp();
+                        mbar_arrive_lane0(empty + rp.slot, lane);
+                        ring_next(rp, D);
+                        jr = 0;
                     }
                 }
             };
@@ -1012,9 +1017,9 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
             // flight, eight partial sums as at entry; the same from the U stage)
             const T *Ut = p.pd.Ut + B.offU;
             if (ust) {
-                // two of the lane's data points at a time (m, m + S)
-                for (int m = sl; m < p.M; m += 2 * S) {
-                    const bool two = m + S < p.M;
+                // two of the lane's data points at a time (m, m + S; one in the widest tiles)
+                for (int m = sl; m < p.M; m += (KV <= 8 ? 2 : 1) * S) {
+                    const bool two = KV <= 8 && m + S < p.M;
                     const int m2 = two ? m + S : m;
                     T a[8], b[8];
 #pragma unroll
@@ -1090,6 +1095,9 @@ __device__ __forceinline__ void consume(const SweepParams<T> &p, const LaunchSha
                             }
                         }
                     }
+                    // one chunk's sums at a time: keeps the compiler from holding every
+                    // chunk's loaded sums in registers at once (the widest tiles spilled)
+                    if (v + 1 == VEC) asm volatile("" ::: "memory");
                 }
             __syncwarp();
         }

@@ -65,9 +65,9 @@ def test_grid_sweep_largest_grid_against_oracle():
     the oracle's factors.  At this size 200 sweeps do not reach equilibrium:
     runs in two mode bases (the library's SVD and the oracle's) are two Markov
     chains with the same stationary law but different transients, which the
-    standard errors do not measure (oracle against oracle with different level
-    schedules differs by tens of standard errors here); in the oracle's basis
-    and on its level schedule both sides run the same chain."""
+    standard errors do not measure (runs on different level schedules differ by
+    tens of standard errors here); in the oracle's basis and on its level
+    schedule both sides run the same chain."""
     z, l2, l2_se = _compare(2000, "uniform", 1024, 128, 200, 300, 56, oracle_factors=True)
     assert np.max(z) < Z_MAX, float(np.max(z))
     assert 0.75 < np.mean(z ** 2) < 1.33, float(np.mean(z ** 2))
