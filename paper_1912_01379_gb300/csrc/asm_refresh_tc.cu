@@ -12,7 +12,14 @@
 // r_ref = g~ - K~ fref formed in FP64 once per refresh: K~ A is of the size of
 // the posterior spread, and its FP32 accumulation error shrinks with it.  The
 // difference f - fref is formed exactly in FP64 before the split into TF32
-// high and FP32 low parts.
+// high and low parts.
+//
+// Split.  Both parts are rounded to the nearest TF32 value here, so that the
+// MMA, which reads 10 mantissa bits of each operand, takes them exactly: a
+// high part off by at most 2^-11 of x and a low part off by at most 2^-11 of
+// the remainder, i.e. 2^-22 of x.  Left to the MMA's truncation the low part
+// would lose up to 2^-21 of x.  With the dropped A_lo K_lo term each product
+// K~_mn A_n then carries at most about 3 2^-22 of its size.
 //
 // One CTA of 128 threads owns 128 chains of one problem (the MMA's M = 128
 // rows, one TMEM lane per chain) and loops over the problem's M_tau tiles
@@ -95,7 +102,7 @@ __device__ __forceinline__ float tf32_round(float x)
 // Stages rows [row0, row0 + nrows) x columns [k0, k0 + 32) of a row-major FP32
 // matrix (leading dimension ld, a multiple of 4; rows >= rows_valid and columns
 // >= cols_valid read as 0) into the layout [row/8][k/4][row%8][k%4].  With
-// `lo` the TF32 high part goes to hi and the remainder to lo.
+// `lo` the TF32 high part goes to hi and the remainder, rounded to TF32, to lo.
 __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int ld, int rows_valid, int cols_valid,
                                            int row0, int k0, int nrows, unsigned char *hi, unsigned char *lo)
 {
@@ -115,7 +122,8 @@ __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int ld
         if (lo) {
             const float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
             *reinterpret_cast<float4 *>(hi + off) = h;
-            *reinterpret_cast<float4 *>(lo + off) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+            *reinterpret_cast<float4 *>(lo + off) = make_float4(tf32_round(v.x - h.x), tf32_round(v.y - h.y),
+                                                                tf32_round(v.z - h.z), tf32_round(v.w - h.w));
         } else {
             *reinterpret_cast<float4 *>(hi + off) = v;
         }
@@ -123,7 +131,7 @@ __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int ld
 }
 
 // The same layout for the centred chain states: rows of f - fref, the
-// difference exact in FP64, split into a TF32 high part and an FP32 remainder.
+// difference exact in FP64, split into TF32 high and low parts.
 __device__ __forceinline__ void stage_centred(const float *__restrict__ F, int ld, const float *__restrict__ fref,
                                               int rows_valid, int cols_valid, int row0, int k0, unsigned char *hi,
                                               unsigned char *lo)
@@ -148,7 +156,7 @@ __device__ __forceinline__ void stage_centred(const float *__restrict__ F, int l
         for (int j = 0; j < 4; ++j) {
             const double d = (double)x[j] - (double)c[j];
             h[j] = tf32_round((float)d);
-            l[j] = (float)(d - (double)h[j]);
+            l[j] = tf32_round((float)(d - (double)h[j]));
         }
         const int off = (rg * 8 + kc) * 128 + r8 * 16;
         *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
@@ -313,7 +321,7 @@ __global__ void split_k_kernel(const double *__restrict__ KtT, int M, int N, int
     const double x = n < N ? KtT[(size_t)n * M + m] : 0.0;
     const float h = tf32_round((float)x);
     Khi[i] = h;
-    Klo[i] = (float)(x - (double)h);
+    Klo[i] = tf32_round((float)(x - (double)h));
 }
 
 }  // namespace
