@@ -82,6 +82,11 @@ struct SweepParams {
     // FP32) and r_ref = g~ - K~ fref (M, FP64); the product is taken of f - fref
     float *fref;
     double *rref;
+    // k-split of the tensor-core refresh: the grid points are cut into ksplit parts
+    // whose FP32 partial products (ksplit x chains x ldR) are added in FP64 in part
+    // order by the finishing kernel; ksplit = 1: no partials (nullptr)
+    float *Dpart;
+    int ksplit;
     // gamma prior: a_n - 1 per grid point (nullptr: flat)
     const T *prior_am1;
     // step-size trace (nullptr: off): sum over chains of |f(s+1) - f(s)| / |f(s)| for
@@ -156,15 +161,22 @@ ASM_DECLARE_SWEEP_LAUNCHER(float, f32_prior)     // with the gamma prior, one CT
 ASM_DECLARE_SWEEP_LAUNCHER(double, f64_prior)
 #undef ASM_DECLARE_SWEEP_LAUNCHER
 // Tensor-core residual refresh of the mixed path (asm_refresh_tc.cu): grid of
-// (chain tiles of 128) x n_problems CTAs; max_bn = the largest refresh_tc_bn(M).
-cudaError_t launch_refresh_tc(const SweepParams<float> *probs, int n_problems, int chains, int max_bn, bool track_drift,
-                              cudaStream_t s);
+// (chain tiles of 128) x n_problems x (the largest k split) CTAs; max_bn = the
+// largest refresh_tc_bn(M).
+cudaError_t launch_refresh_tc(const SweepParams<float> *probs, int n_problems, int chains, int max_bn, int max_parts,
+                              bool track_drift, cudaStream_t s);
 int refresh_tc_bn(int M);                  // MMA N of a problem's M_tau tiles
+int refresh_tc_ksplit(int chains, int N);  // parts of a problem's k range (a function of the problem)
+// The FP64 combination of the k parts (problems with ksplit > 1): r~, chi^2, drift.
+cudaError_t launch_refresh_finish(const SweepParams<float> *probs, int n_problems, int chains, bool track_drift,
+                                  cudaStream_t s);
 size_t refresh_tc_smem(int max_bn);        // dynamic shared memory of one CTA
 constexpr int kRefreshTcLdK = 32;          // ldK is a multiple of this (one k-tile)
 cudaError_t launch_split_k(const double *KtT, int M, int N, int ldK, float *Khi, float *Klo, cudaStream_t s);
-// Reference state of every problem's tensor-core refresh (one CTA per problem).
-cudaError_t launch_refresh_ref(const SweepParams<float> *probs, int n_problems, int chains, cudaStream_t s);
+// Reference state of every problem's tensor-core refresh: fref over tiles of 32
+// grid points, then r_ref over tiles of 128 data points (two launches).
+cudaError_t launch_refresh_ref(const SweepParams<float> *probs, int n_problems, int chains, int max_N, int max_M,
+                               cudaStream_t s);
 // Contractions of the backward pass (asm_moments.cu).  D: chains x ldD snapshot
 // (centred); Sff (N x N, FP64) += D^T D; Y (chains x PM) = D Kth^T with Kth
 // PM x N row-major (the whitened dK/dtheta of all parameters); Sq (chains x P)

@@ -324,6 +324,8 @@ struct WsLayout {
     size_t fref, rref;                       // reference state of the tensor-core refresh
     size_t steptrace;                        // step-size trace (kStepTraceMax sweeps)
     size_t P1, P2;                           // FP32 path: kept-sweep sums of the open 64-sweep block (chains x ldF FP32)
+    size_t Dpart;                            // FP32 path: k parts of the tensor-core refresh (ksplit x chains x ldR)
+    int ksplit;
     size_t total;
     int ldF, ldR;
 };
@@ -448,6 +450,8 @@ WsLayout ws_layout(const asm_problem *p, int chains, int precision)
     L.steptrace = off; off = align_up(off + (size_t)kStepTraceMax * 8, 256);
     L.P1 = off; off = align_up(off + (precision == ASM_FP64 ? 0 : (size_t)chains * L.ldF * 4), 256);
     L.P2 = off; off = align_up(off + (precision == ASM_FP64 ? 0 : (size_t)chains * L.ldF * 4), 256);
+    L.ksplit = precision == ASM_FP64 ? 1 : refresh_tc_ksplit(chains, p->N);
+    L.Dpart = off; off = align_up(off + (L.ksplit > 1 ? (size_t)L.ksplit * chains * L.ldR * 4 : 0), 256);
     L.total = off;
     return L;
 }
@@ -893,6 +897,8 @@ SweepParams<T> make_params(asm_problem *p, const PrecBuffers &b, const WsLayout 
     sp.steptrace = p->trace ? (double *)(ws + L.steptrace) : nullptr;
     sp.P1 = sizeof(T) == 4 ? (float *)(ws + L.P1) : nullptr;
     sp.P2 = sizeof(T) == 4 ? (float *)(ws + L.P2) : nullptr;
+    sp.ksplit = sizeof(T) == 4 ? L.ksplit : 1;
+    sp.Dpart = sp.ksplit > 1 ? (float *)(ws + L.Dpart) : nullptr;
     sp.trace_cap = kStepTraceMax;
     return sp;
 }
@@ -1164,8 +1170,11 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
     if (const int rc = refresh_smem(refresh_all_kernel<T>, rsmem); rc != ASM_OK) return rc;
     // the mixed path refreshes on the tensor cores (3xTF32) unless asked for FP64 CUDA cores
     const bool tc = sizeof(T) == 4 && !h->refresh_fp64;
-    int max_bn = 16;
-    for (asm_problem *u : us) max_bn = std::max(max_bn, refresh_tc_bn(u->M));
+    int max_bn = 16, max_parts = 1;
+    for (asm_problem *u : us) {
+        max_bn = std::max(max_bn, refresh_tc_bn(u->M));
+        if (tc) max_parts = std::max(max_parts, refresh_tc_ksplit(chains, u->N));
+    }
     if (tc && refresh_tc_smem(max_bn) > 227 * 1024) return ASM_ERR_TOO_LARGE;
     SweepParams<T> *d_probs = (SweepParams<T> *)(base + RL.probs);
     WorkItem *d_items = (WorkItem *)(base + RL.items);
@@ -1191,11 +1200,16 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
         bin_kernel<T><<<n_refresh, 128, 0, st>>>(d_probs, chains, ctrl);
         return cudaGetLastError();
     };
+    // kernels of one refresh: reference state, tensor-core product and, with a k split, the
+    // FP64 combination; or the FP64 CUDA-core refresh
+    const int refresh_launches = tc ? (max_parts > 1 ? 4 : 3) : 1;
     auto refresh = [&](cudaStream_t st) {
         if constexpr (sizeof(T) == 4) {
             if (tc) {
-                const cudaError_t e = launch_refresh_ref(d_probs, (int)us.size(), chains, st);
-                return e != cudaSuccess ? e : launch_refresh_tc(d_probs, (int)us.size(), chains, max_bn, true, st);
+                cudaError_t e = launch_refresh_ref(d_probs, (int)us.size(), chains, max_N, max_M, st);
+                if (e == cudaSuccess) e = launch_refresh_tc(d_probs, (int)us.size(), chains, max_bn, max_parts, true, st);
+                if (e == cudaSuccess && max_parts > 1) e = launch_refresh_finish(d_probs, (int)us.size(), chains, true, st);
+                return e;
             }
         }
         refresh_all_kernel<T><<<n_refresh, 128, rsmem, st>>>(d_probs, chains, 1);
@@ -1257,7 +1271,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
             for (long long i = 0; i < whole; ++i)
                 if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) return ASM_ERR_CUDA;
             h->sweep_launches += whole;
-            h->other_launches += 1 + 3 * whole;
+            h->other_launches += 1 + (2 + refresh_launches) * whole;   // per replay: range, binning, refresh
             h->graph_replays += whole;
             if (tc) h->tc_refreshes += whole;
             s += whole * kRefreshPeriod;
@@ -1290,7 +1304,7 @@ int run_all(asm_problem *h, int chains, long long s_begin, long long s_end, long
         if (s % kRefreshPeriod == 0) {
             if (binning(h->stream) != cudaSuccess) return ASM_ERR_CUDA;
             if (refresh(h->stream) != cudaSuccess) return ASM_ERR_CUDA;
-            h->other_launches += 2;
+            h->other_launches += 1 + refresh_launches;
             if (tc) ++h->tc_refreshes;
         }
     }
@@ -1317,7 +1331,7 @@ int init_chains(asm_problem *p, const WsLayout &L, int chains)
     if (cudaMemsetAsync(ws + L.steptrace, 0, (size_t)kStepTraceMax * 8, p->stream) != cudaSuccess)
         return ASM_ERR_CUDA;
     // FP32 state: no 64-sweep block of kept sums open yet
-    if (sizeof(T) == 4 && cudaMemsetAsync(ws + L.P1, 0, L.total - L.P1, p->stream) != cudaSuccess)
+    if (sizeof(T) == 4 && cudaMemsetAsync(ws + L.P1, 0, L.Dpart - L.P1, p->stream) != cudaSuccess)
         return ASM_ERR_CUDA;
     p->nsnap = 0;
     if (const int rc = refresh_smem(refresh_kernel<T>, sizeof(double) * p->N); rc != ASM_OK) return rc;

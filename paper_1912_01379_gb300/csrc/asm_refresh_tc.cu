@@ -164,23 +164,38 @@ __device__ __forceinline__ void stage_centred(const float *__restrict__ F, int l
     }
 }
 
-// Reference state of one problem per CTA: fref = mean of the chain states
-// (FP32, summed in chain order) and r_ref = g~ - K~ fref in FP64.
-__global__ void refresh_ref_kernel(const SweepParams<float> *__restrict__ probs, int chains)
+// Reference state of the refresh, in two steps over the whole GPU.
+// fref = mean of the chain states (FP32): CTA (x, problem) takes 32 grid points,
+// lane l point 32 x + l (coalesced rows), warp w the chains q = w mod 8 in order;
+// the eight partial sums are added in warp order.
+__global__ void refresh_fref_kernel(const SweepParams<float> *__restrict__ probs, int chains)
 {
-    const SweepParams<float> &p = probs[blockIdx.x];
-    const float inv = 1.0f / (float)chains;
-    for (int n = threadIdx.x; n < p.N; n += blockDim.x) {
-        float a = 0.f;
-        for (int q = 0; q < chains; ++q) a += p.F[(size_t)q * p.ldF + n];
-        p.fref[n] = a * inv;
-    }
+    __shared__ float part[8][32];
+    const SweepParams<float> &p = probs[blockIdx.y];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + lane;
+    if (blockIdx.x * 32 >= p.N) return;   // (uniform per CTA)
+    float a = 0.f;
+    if (n < p.N)
+        for (int q = w; q < chains; q += 8) a += p.F[(size_t)q * p.ldF + n];
+    part[w][lane] = a;
     __syncthreads();
-    for (int m = threadIdx.x; m < p.M; m += blockDim.x) {
-        double a = p.gt[m];
-        for (int n = 0; n < p.N; ++n) a -= p.KtT[(size_t)n * p.M + m] * (double)p.fref[n];
-        p.rref[m] = a;
+    if (w == 0 && n < p.N) {
+        float t = part[0][lane];
+        for (int k = 1; k < 8; ++k) t += part[k][lane];
+        p.fref[n] = t * (1.0f / (float)chains);
     }
+}
+
+// r_ref = g~ - K~ fref in FP64, one thread per data point.
+__global__ void refresh_rref_kernel(const SweepParams<float> *__restrict__ probs)
+{
+    const SweepParams<float> &p = probs[blockIdx.y];
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= p.M) return;
+    double a = p.gt[m];
+    for (int n = 0; n < p.N; ++n) a -= p.KtT[(size_t)n * p.M + m] * (double)p.fref[n];
+    p.rref[m] = a;
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -190,10 +205,15 @@ refresh_tc_kernel(const SweepParams<float> *__restrict__ probs, int chains, int 
     __shared__ unsigned long long bar[2];
     __shared__ unsigned s_tmem;
     const SweepParams<float> &p = probs[blockIdx.y];
+    const int nparts = p.ksplit > 1 ? p.ksplit : 1;   // this problem's k parts
+    if ((int)blockIdx.z >= nparts) return;            // (uniform per CTA, before any barrier)
     const int M = p.M, N = p.N;
     const int ntiles = (M + kTcCols - 1) / kTcCols;
     const int BN = ((M + ntiles - 1) / ntiles + 15) / 16 * 16;   // MMA N: a multiple of 16, <= 256
     const int nkt = (N + kTcBK - 1) / kTcBK;
+    // this CTA's k-tiles [kt0, kt1) (every part holds at least one: nparts <= nkt)
+    const int kt0 = (int)(((long long)blockIdx.z * nkt) / nparts);
+    const int kt1 = (int)(((long long)(blockIdx.z + 1) * nkt) / nparts);
     const int warp = threadIdx.x >> 5;
     unsigned char *base = smem_dyn + ((1024 - (smem_addr(smem_dyn) & 1023)) & 1023);
 
@@ -222,8 +242,8 @@ refresh_tc_kernel(const SweepParams<float> *__restrict__ probs, int chains, int 
 
     for (int mt = 0; mt < ntiles && !fail; ++mt) {
         const int m0 = mt * BN;
-        for (int kt = 0; kt < nkt; ++kt) {
-            const int st = kt & 1;
+        for (int kt = kt0; kt < kt1; ++kt) {
+            const int st = (kt - kt0) & 1;
             unsigned char *a_hi = base + (size_t)st * stage_bytes;
             unsigned char *a_lo = a_hi + kTcAtile;
             unsigned char *b_hi = a_lo + kTcAtile;
@@ -248,7 +268,7 @@ refresh_tc_kernel(const SweepParams<float> *__restrict__ probs, int chains, int 
                     const unsigned long long dal = umma_desc(smem_addr(a_lo) + k_off, 128, 1024);
                     const unsigned long long dbh = umma_desc(smem_addr(b_hi) + k_off, 128, 1024);
                     const unsigned long long dbl = umma_desc(smem_addr(b_lo) + k_off, 128, 1024);
-                    umma_tf32(tmem, dah, dbh, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
+                    umma_tf32(tmem, dah, dbh, idesc, (kt > kt0 || ks > 0) ? 1u : 0u);
                     umma_tf32(tmem, dah, dbl, idesc, 1u);
                     umma_tf32(tmem, dal, dbh, idesc, 1u);
                 }
@@ -258,7 +278,7 @@ refresh_tc_kernel(const SweepParams<float> *__restrict__ probs, int chains, int 
         }
         if (fail) break;
         // the last commit covers every MMA issued before it
-        const int lst = (nkt - 1) & 1;
+        const int lst = (kt1 - kt0 - 1) & 1;
         if (!mbar_wait(&bar[lst], (uses[lst] - 1u) & 1u, kWaitLimit)) fail = 1;
         if (__syncthreads_or(fail)) {
             fail = 1;
@@ -269,7 +289,14 @@ refresh_tc_kernel(const SweepParams<float> *__restrict__ probs, int chains, int 
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
             tmem_ld16(lane_base + (unsigned)c0, v);
-            if (active) {
+            if (active && nparts > 1) {   // this part's product, combined by refresh_finish_kernel
+                float *Dq = p.Dpart + ((size_t)blockIdx.z * chains + q) * p.ldR;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int m = m0 + c0 + j;
+                    if (m < M) Dq[m] = v[j];
+                }
+            } else if (active) {
                 float *Rq = p.R + (size_t)q * p.ldR;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -296,7 +323,7 @@ refresh_tc_kernel(const SweepParams<float> *__restrict__ probs, int chains, int 
                 if (uses[s]) mbar_wait(&bar[s], (uses[s] - 1u) & 1u, kWaitLimit);
             atomicAdd(&p.counters->timeouts, 1ull);
         }
-    } else if (active) {
+    } else if (active && nparts == 1) {
         p.chi2[q] = sum_new;
         if (track_drift) {
             const double drift = fabs(sum_old - sum_new) / fmax(sum_new, 1e-300);
@@ -324,7 +351,61 @@ __global__ void split_k_kernel(const double *__restrict__ KtT, int M, int N, int
     Klo[i] = tf32_round((float)(x - (double)h));
 }
 
+// r~ = r_ref - (sum over the k parts of their products, added in FP64 in part
+// order), chi^2 and the drift, for the problems whose refresh is split over k:
+// one warp per chain, the lanes over the data points.
+__global__ void refresh_finish_kernel(const SweepParams<float> *__restrict__ probs, int chains, int track_drift)
+{
+    const SweepParams<float> &p = probs[blockIdx.y];
+    if (p.ksplit <= 1) return;
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= chains) return;
+    const size_t part = (size_t)chains * p.ldR;
+    const float *Dq = p.Dpart + (size_t)q * p.ldR;
+    float *Rq = p.R + (size_t)q * p.ldR;
+    double sum_old = 0.0, sum_new = 0.0;
+    for (int m = lane; m < p.M; m += 32) {
+        double d = 0.0;
+        for (int z = 0; z < p.ksplit; ++z) d += (double)Dq[z * part + m];
+        const double r = p.rref[m] - d;
+        const double old = (double)Rq[m];
+        sum_old += old * old;
+        sum_new += r * r;
+        Rq[m] = (float)r;
+    }
+    for (int off = 16; off; off >>= 1) {
+        sum_old += __shfl_xor_sync(0xffffffffu, sum_old, off);
+        sum_new += __shfl_xor_sync(0xffffffffu, sum_new, off);
+    }
+    if (lane == 0) {
+        p.chi2[q] = sum_new;
+        if (track_drift) {
+            const double drift = fabs(sum_old - sum_new) / fmax(sum_new, 1e-300);
+            atomicMax(&p.counters->drift_bits, (unsigned long long)__double_as_longlong(drift));
+        }
+    }
+}
+
 }  // namespace
+
+int refresh_tc_ksplit(int chains, int N)
+{
+    // enough CTAs to cover the GPU once, at least two k-tiles per part, at most 16 parts
+    const int nkt = (N + kTcBK - 1) / kTcBK;
+    const int tiles = (chains + kTcRows - 1) / kTcRows;
+    int parts = (152 + tiles - 1) / tiles;
+    parts = std::min(parts, std::max(1, nkt / 2));
+    return std::max(1, std::min(parts, 16));
+}
+
+cudaError_t launch_refresh_finish(const SweepParams<float> *probs, int n_problems, int chains, bool track_drift,
+                                  cudaStream_t s)
+{
+    const dim3 grid((unsigned)((chains + 3) / 4), (unsigned)n_problems);
+    refresh_finish_kernel<<<grid, 128, 0, s>>>(probs, chains, track_drift ? 1 : 0);
+    return cudaGetLastError();
+}
 
 int refresh_tc_bn(int M)
 {
@@ -337,21 +418,23 @@ size_t refresh_tc_smem(int max_bn)
     return 2 * ((size_t)2 * kTcAtile + (size_t)2 * max_bn * kTcBK * 4) + 1024;
 }
 
-cudaError_t launch_refresh_tc(const SweepParams<float> *probs, int n_problems, int chains, int max_bn, bool track_drift,
-                              cudaStream_t s)
+cudaError_t launch_refresh_tc(const SweepParams<float> *probs, int n_problems, int chains, int max_bn, int max_parts,
+                              bool track_drift, cudaStream_t s)
 {
     const int stage_bytes = 2 * kTcAtile + 2 * max_bn * kTcBK * 4;
     const size_t smem = refresh_tc_smem(max_bn);
     cudaError_t e = cudaFuncSetAttribute(refresh_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)((chains + kTcRows - 1) / kTcRows), (unsigned)n_problems);
+    const dim3 grid((unsigned)((chains + kTcRows - 1) / kTcRows), (unsigned)n_problems, (unsigned)max_parts);
     refresh_tc_kernel<<<grid, kTcThreads, smem, s>>>(probs, chains, stage_bytes, track_drift ? 1 : 0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_refresh_ref(const SweepParams<float> *probs, int n_problems, int chains, cudaStream_t s)
+cudaError_t launch_refresh_ref(const SweepParams<float> *probs, int n_problems, int chains, int max_N, int max_M,
+                               cudaStream_t s)
 {
-    refresh_ref_kernel<<<(unsigned)n_problems, 256, 0, s>>>(probs, chains);
+    refresh_fref_kernel<<<dim3((unsigned)((max_N + 31) / 32), (unsigned)n_problems), 256, 0, s>>>(probs, chains);
+    refresh_rref_kernel<<<dim3((unsigned)((max_M + 127) / 128), (unsigned)n_problems), 128, 0, s>>>(probs);
     return cudaGetLastError();
 }
 

@@ -9,8 +9,9 @@ ids; <fbar> must agree within 4 combined standard errors at every grid point
 oracle chain means, so that each standard error is itself estimated to a few
 per cent).  The relative L2 error of <A> is checked against the same combined
 error.  The largest grid, N_omega = 2000, is compared the same way, with the
-distribution of the z-scores checked as well (mean square near 1, no more
-than 1 % beyond 3).
+4-sigma rule applied per point (at most the two points that chance allows
+beyond 4 in 2000, none beyond 5) and the distribution of the z-scores checked
+as well (mean square near 1, no more than 1 % beyond 3).
 """
 import numpy as np
 import pytest
@@ -69,7 +70,13 @@ def test_grid_sweep_largest_grid_against_oracle():
     tens of standard errors here); in the oracle's basis and on its level
     schedule both sides run the same chain."""
     z, l2, l2_se = _compare(2000, "uniform", 1024, 128, 200, 300, 56, oracle_factors=True)
-    assert np.max(z) < Z_MAX, float(np.max(z))
+    # 4 standard errors per point over 2000 points: independent normal z-scores exceed 4 at
+    # 0.13 points on average (a max-over-the-grid test would fail a correct sampler about one
+    # run in eight), so at most two points may, and none may exceed 5 (2000 points x P(|z| > 5)
+    # = 1e-3); the 128 oracle chain means are skewed where the spectrum peaks, which fattens
+    # the tails a little
+    assert np.sum(z > Z_MAX) <= 2, (int(np.sum(z > Z_MAX)), float(np.max(z)))
+    assert np.max(z) < 5.0, float(np.max(z))
     assert 0.75 < np.mean(z ** 2) < 1.33, float(np.mean(z ** 2))
     assert np.mean(z > 3.0) <= 0.01, float(np.mean(z > 3.0))
     assert l2 < 3.0 * l2_se, (l2, l2_se)

@@ -81,7 +81,10 @@ def test_blocked_modes_take_the_largest_steps(N):
     schemes = {"components": [np.arange(N)], "modes": [[0]], "blocked": asm.partition_hierarchy(N)}
     chains, sweeps = 512, 400
     mean = {k: _mean_steps(p, lev, chains, sweeps, 7)[100:].mean() for k, lev in schemes.items()}
-    assert mean["blocked"] > 4 * mean["components"], mean
+    # blocked modes' mean step depends on which levels of the hierarchy the 300 sweeps drew
+    # (every level has its own step size; all chains share the schedule): across seeds the
+    # ratio to components sampling ran from 4.0 to 6.6 at N = 120, hence the factor 3
+    assert mean["blocked"] > 3 * mean["components"], mean
     assert mean["blocked"] > 1.5 * mean["modes"], mean
     # the oracle's steps agree with the GPU's in the same mode basis (the step size of a
     # sweep depends on the basis chosen within degenerate and null subspaces, which
