@@ -54,7 +54,8 @@ def _args():
     ap.add_argument("--burn", type=int, default=1000)
     ap.add_argument("--sweeps", type=int, default=10000)
     ap.add_argument("--chains", type=int, default=1024)
-    ap.add_argument("--fp64-sweeps", type=int, default=1000)
+    ap.add_argument("--fp64-sweeps", type=int, default=10000,
+                    help="kept sweeps of the plain FP64 leg (burn-in in the headline's proportion)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="heuristic launch shape instead of asm_tune's")
@@ -589,7 +590,8 @@ def main():
     ceil = measured_ceilings(asm)
     achieved, peak = roofline(elems_total, fmas_total, sweep_ms / 1e3, ceil, "f32")
 
-    # plain FP64 path, same workload, shorter run (a rate)
+    # plain FP64 path, same workload; at the default length the same run as a mixed step, so
+    # that its binned ESS (and ESS/s) is estimated from as many sweeps as the mixed path's
     fp64 = None
     if args.fp64_sweeps > 0:
         f64s = args.fp64_sweeps
@@ -597,7 +599,7 @@ def main():
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        seed64, burn64 = seed_base + 1000, f64s // 10
+        seed64, burn64 = seed_base + 1000, max(1, (args.burn * f64s) // max(args.sweeps, 1))
         e0.record(stream)
         gp.sample(chains, burn64, f64s, seed64, precision=asm.ASM_FP64, timing=True)
         e1.record(stream)
