@@ -22,9 +22,13 @@
 // K~_mn A_n then carries at most about 3 2^-22 of its size.
 //
 // One CTA of 128 threads owns 128 chains of one problem (the MMA's M = 128
-// rows, one TMEM lane per chain) and loops over the problem's M_tau tiles
-// (N of the MMA, <= 256 columns of FP32 accumulator) and over k-tiles of 32
-// grid points.  Each k-tile is staged by all threads into shared memory in
+// rows, one TMEM lane per chain) and one part of its grid points, and loops over
+// the problem's M_tau tiles (N of the MMA, <= 256 columns of FP32 accumulator)
+// and over the part's k-tiles of 32 grid points.  The parts (refresh_tc_ksplit:
+// enough CTAs to cover the GPU, a function of the problem alone) keep each FP32
+// accumulation short; with more than one, each CTA stores its FP32 product and
+// refresh_finish_kernel adds the parts in FP64 in part order, so the result does
+// not depend on which CTA finishes first.  Each k-tile is staged by all threads into shared memory in
 // the canonical K-major layout without swizzle (core matrices of 8 rows x 16
 // bytes), A split into TF32 high and low parts on the way; K~ comes split
 // from set-up.  Two stages alternate: thread 0 issues the 12 tcgen05.mma of a
