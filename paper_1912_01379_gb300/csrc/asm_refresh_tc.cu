@@ -28,10 +28,10 @@
 // enough CTAs to cover the GPU, a function of the problem alone) keep each FP32
 // accumulation short; with more than one, each CTA stores its FP32 product and
 // refresh_finish_kernel adds the parts in FP64 in part order, so the result does
-// not depend on which CTA finishes first.  Each k-tile is staged by all threads into shared memory in
-// the canonical K-major layout without swizzle (core matrices of 8 rows x 16
-// bytes), A split into TF32 high and low parts on the way; K~ comes split
-// from set-up.  Two stages alternate: thread 0 issues the 12 tcgen05.mma of a
+// not depend on which CTA finishes first.  Each k-tile is staged by all
+// threads into shared memory in the canonical K-major layout without swizzle
+// (core matrices of 8 rows x 16 bytes), A split into TF32 high and low parts on
+// the way; K~ comes split from set-up.  Two stages alternate: thread 0 issues the 12 tcgen05.mma of a
 // stage and commits them to the stage's mbarrier, which the threads wait on
 // before staging into it again.  Waits are bounded (timeouts are counted).
 #include "asm_sweep.cuh"
