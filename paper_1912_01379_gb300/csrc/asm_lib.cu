@@ -190,6 +190,21 @@ __global__ void bin_reduce_kernel(const double *__restrict__ acc1, const double 
     out[(size_t)kBinLevels * N + i] = b;
 }
 
+// FP32 state: the sums of the open 64-sweep block added to the FP64 sums now
+// and cleared.  Used when a continuation starts a new burn-in: the kept run is
+// broken, and the block's earlier kept sweeps must be in S1 before the next bin
+// boundary, where the binning takes S1's growth over the bin as the bin's sum.
+__global__ void fold_open_block_kernel(float *P1, float *P2, int ldP, double *S1, double *S2, int chains, int N)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)chains * N) return;
+    const long long q = i / N, n = i % N;
+    S1[i] += (double)P1[q * ldP + n];
+    S2[i] += (double)P2[q * ldP + n];
+    P1[q * ldP + n] = 0.f;
+    P2[q * ldP + n] = 0.f;
+}
+
 // Per grid point: mean over chains and kept sweeps, the spread of the chain
 // means (two passes) and the second moment.  P1, P2 (FP32 chain state; else
 // null): the kept-sweep sums of a 64-sweep block still open, added here.
@@ -1750,6 +1765,19 @@ int asm_sample(asm_problem *p, int chains, long burn_in, long sweeps, uint64_t s
         if (rc != ASM_OK) return rc;
     }
     const long long s0 = p->sweeps_done, s1 = s0 + burn_in + sweeps;
+    if (cont && burn_in > 0 && precision == ASM_MIXED && s0 % kBinSweeps != 0) {
+        // a new burn-in inside an open 64-sweep block: its earlier kept sweeps go to the FP64 sums now
+        for (asm_problem *u : units_of(p)) {
+            const WsLayout L = ws_layout(u, chains, precision);
+            char *ws = (char *)u->ws;
+            const long long tot = (long long)chains * u->N;
+            fold_open_block_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, p->stream>>>(
+                (float *)(ws + L.P1), (float *)(ws + L.P2), L.ldF, (double *)(ws + L.S1), (double *)(ws + L.S2),
+                chains, u->N);
+            ++u->other_launches;
+        }
+        if (cudaGetLastError() != cudaSuccess) return ASM_ERR_CUDA;
+    }
     // first sweep of the unbroken run of kept sweeps: a continuation without burn-in
     // extends the previous one (bins may straddle the calls)
     long long burn_abs = s0 + burn_in;

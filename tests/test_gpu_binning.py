@@ -91,3 +91,24 @@ def test_batch_problem_error_equals_single_handle():
     one.sample(16, 64, 256, 9, precision=asm.ASM_MIXED)
     eb, eo = b.mc_error(1), one.mc_error()
     assert np.array_equal(eb["sem_fbar"], eo["sem_fbar"]) and np.array_equal(eb["ess"], eo["ess"])
+
+
+def test_new_burn_in_inside_an_open_block():
+    """A continuation that starts a new burn-in inside a 64-sweep block: kept
+    sweeps 0..9, then 54 burn-in sweeps and 64 kept ones, so the one complete bin
+    is sweeps 64..127.  The mixed path keeps the open block's sums in FP32 until
+    the block closes; they must reach the FP64 sums before the bin starts, or
+    the bin would also hold sweeps 0..9 and its mean come out (74/64) too large.
+    The level-0 bin variance over the chain-mean variance is then the same in the
+    mixed and the FP64 path (1.08 here for both)."""
+    p = W.small_problem(16, 40, seed=10, levels=[[0], [0, 13, 29]])
+    ratio = {}
+    for prec in (asm.ASM_MIXED, asm.ASM_FP64):
+        gp = asm.Problem(p.K, p.G, p.C, p.levels, w=p.w)
+        gp.sample(512, 0, 10, 5, precision=prec)
+        gp.sample(512, 54, 64, 5, precision=prec, cont=True)
+        e, a = gp.mc_error(), gp.average()
+        assert e["bins_per_chain"][0] == 1 and e["bins_per_chain"][1] == 0
+        assert np.all(np.isfinite(a["mean_A"]))
+        ratio[prec] = float(np.nanmean(e["sigma2_levels"][0] / a["sem_fbar"] ** 2))
+    assert abs(ratio[asm.ASM_MIXED] - ratio[asm.ASM_FP64]) < 0.1, ratio
